@@ -1,0 +1,402 @@
+"""Pins of the FP64 oracle to results fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a closed
+form derived from the scheme, a conservation law, a published series or test
+vector, or brute force written here in a different way (numpy enumeration,
+bisection).  They are chosen so that a dropped term, a wrong sign or index, or
+a wrong relaxation rate in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return json.load(fh)
+
+
+# ---------------------------------------------------------------------------
+# D3Q19 lattice and equilibrium (Sec. 2.1, Eq. (equilibrium))
+# ---------------------------------------------------------------------------
+def test_velocity_set_isotropy():
+    e, w = O.velocity_set()
+    assert len({tuple(v) for v in e}) == 19
+    assert abs(w.sum() - 1.0) < 1e-15
+    for k in range(19):
+        assert (e[O.opposite(k)] == -e[k]).all()
+    ef = e.astype(np.float64)
+    # lattice tensors of a c_s^2 = 1/3 model
+    assert np.allclose(np.einsum("k,ka->a", w, ef), 0.0, atol=1e-16)
+    assert np.allclose(np.einsum("k,ka,kb->ab", w, ef, ef), np.eye(3) / 3.0, atol=1e-16)
+    m4 = np.einsum("k,ka,kb,kc,kd->abcd", w, ef, ef, ef, ef)
+    d = np.eye(3)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+           + np.einsum("ad,bc->abcd", d, d)) / 9.0
+    assert np.allclose(m4, iso, atol=1e-16)
+
+
+@pytest.mark.parametrize("rho,u", [(1.0, (0.0, 0.0, 0.0)), (1.02, (0.03, -0.01, 0.02)),
+                                   (0.97, (-0.05, 0.04, 0.0))])
+def test_equilibrium_moments(rho, u):
+    """Incompressible equilibrium: sum f = rho, sum e f = u (rho0 = 1),
+    sum e e f = rho/3 I + u u."""
+    e, _ = O.velocity_set()
+    ef = e.astype(np.float64)
+    feq = O.equilibrium(rho, u)
+    u = np.array(u)
+    assert abs(feq.sum() - rho) < 1e-15
+    assert np.allclose(ef.T @ feq, u, atol=1e-15)
+    pi = np.einsum("k,ka,kb->ab", feq, ef, ef)
+    assert np.allclose(pi, rho / 3.0 * np.eye(3) + np.outer(u, u), atol=1e-15)
+
+
+@pytest.mark.parametrize("tau,lam", [(0.8, 3 / 16), (1.4, 3 / 16), (0.8, 0.25), (0.55, 0.1)])
+def test_relaxation_rates(tau, lam):
+    """1/omega+ = 3 nu + 1/2 and Lambda = (1/omega+ - 1/2)(1/omega- - 1/2)."""
+    op, om, nu = O.rates(tau, lam)
+    assert abs(1.0 / op - (3.0 * nu + 0.5)) < 1e-15
+    assert abs((1.0 / op - 0.5) * (1.0 / om - 0.5) - lam) < 1e-15
+    assert 0.0 < om < 2.0
+    if tau == 0.8 and lam == 3 / 16:
+        assert abs(om - 8.0 / 9.0) < 1e-15
+
+
+def test_splitmix64_published_outputs():
+    g = _golden("splitmix64_seed0.json")
+    out = O.splitmix64(g["seed"], len(g["outputs_hex"]))
+    assert out == [int(h, 16) for h in g["outputs_hex"]]
+
+
+# ---------------------------------------------------------------------------
+# Closed-form steady states of a body-force-driven channel.
+#
+# For the linear (Stokes) regime the TRT steady state in a channel is an exact
+# parabola in the bulk, u'' = -g/nu.  Expanding the bulk populations of that
+# parabola and inserting them into Eq. (CLI) at a wall whose surface lies at
+# the fraction q of the link gives the wall velocity
+#     u(z_w) = -(g/nu) (q^2/2 - 2 Lambda/3)
+# for the velocity u = j + g/2.  With q = 1/2 (Eq. (noslip)) and
+# Lambda = 3/16 it vanishes: the exact half-way wall quoted in Sec. 2.1.
+# ---------------------------------------------------------------------------
+def _channel(nz, tau, lam, q_lo, q_hi, g=1e-6):
+    lat = O.Lattice(2, 2, nz, False, (), tau, lam, (g, 0.0, 0.0), q_lo, q_hi).init()
+    H = nz - 2
+    lat.step(int(40 * H * H / (math.pi ** 2 * lat.nu)) + 200)
+    _, u = lat.moments()
+    ux = u[0, 1:nz - 1, 0, 0]
+    z = np.arange(1, nz - 1, dtype=np.float64)
+    za, zb, nu = 1.0 - q_lo, (nz - 2) + q_hi, lat.nu
+    ua = -(g / nu) * (q_lo ** 2 / 2 - 2 * lam / 3)
+    ub = -(g / nu) * (q_hi ** 2 / 2 - 2 * lam / 3)
+    exact = g / (2 * nu) * (z - za) * (zb - z) + ua + (ub - ua) * (z - za) / (zb - za)
+    return lat, ux, exact, u
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.4])
+def test_poiseuille_half_way_exact(tau):
+    """Sec. 2.1: Lambda = 3/16 puts bounce-back walls exactly half-way."""
+    lat, ux, exact, u = _channel(18, tau, 3 / 16, 0.5, 0.5)
+    assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
+    # no cross-flow, and the profile is the same in every column
+    assert np.max(np.abs(u[1:])) < 1e-15
+    assert np.max(np.abs(u[0] - u[0, :, :1, :1])) < 1e-18
+
+
+@pytest.mark.parametrize("tau,lam,q_lo,q_hi", [
+    (0.8, 0.25, 0.5, 0.5),     # bounce-back, Lambda = 1/4: slip g/(24 nu)
+    (0.8, 3 / 16, 0.3, 0.8),   # CLI off-grid walls
+    (1.4, 3 / 16, 0.3, 0.8),   # same walls, other viscosity: same q-dependence
+    (1.4, 0.25, 0.15, 1.0),    # CLI at q = 1 and small q
+    (0.7, 0.1, 0.05, 0.65),
+])
+def test_channel_wall_slip_closed_form(tau, lam, q_lo, q_hi):
+    lat, ux, exact, _ = _channel(18, tau, lam, q_lo, q_hi)
+    assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
+
+
+def test_cli_second_order_in_resolution():
+    """CLI with Lambda = 3/16 is second order (Sec. 2.2): the deviation from the
+    continuum parabola with walls at the true surfaces falls by ~4 per halving."""
+    errs = []
+    for H in (8, 16, 32):
+        nz = H + 2
+        _, ux, _, _ = _channel(nz, 1.4, 3 / 16, 0.3, 0.8)
+        z = np.arange(1, nz - 1, dtype=np.float64)
+        za, zb = 0.7, H + 0.8
+        nu = (1.4 - 0.5) / 3
+        cont = 1e-6 / (2 * nu) * (z - za) * (zb - z)
+        errs.append(np.max(np.abs(ux - cont)) / np.max(cont))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_slit_permeability():
+    """Eq. (Darcy) on a slit of width H with exact half-way walls.  The plane
+    average samples the parabola at the H fluid nodes (a midpoint sum), so
+    K = nu <u>/g = (1/H) sum_t t (H - t) / 2 over t = 1/2, 3/2, ... = H^2/12 + 1/24
+    (the continuum slit value H^2/12 plus the midpoint-rule term)."""
+    nz, H = 18, 16
+    lat, _, _, _ = _channel(nz, 0.8, 3 / 16, 0.5, 0.5)
+    k_exact = H * H / 12.0 + 1.0 / 24.0
+    k = lat.permeability(1, nz - 2)
+    assert abs(k - k_exact) <= 1e-9 * k_exact
+    # whole box: the wall planes carry no flow
+    assert abs(lat.permeability() - k_exact * H / nz) <= 1e-9 * k_exact
+
+
+# ---------------------------------------------------------------------------
+# Conservation and invariants
+# ---------------------------------------------------------------------------
+def test_periodic_mass_and_momentum():
+    """No walls: the collision conserves mass and momentum and the source adds
+    exactly g per cell and step (sum_k 3 w_k e_k (e_k.g) = g)."""
+    rng = np.random.default_rng(7)
+    nx, ny, nz = 6, 5, 4
+    g = np.array([1e-5, -2e-5, 3e-5])
+    u0 = 0.02 * rng.standard_normal((3, nz, ny, nx))
+    lat = O.Lattice(nx, ny, nz, True, (), 0.8, 3 / 16, g).init(u0)
+    f0 = lat.get_f()
+    e, _ = O.velocity_set()
+    n = nx * ny * nz
+    m0 = f0.sum()
+    j0 = np.einsum("kzyx,ka->a", f0, e.astype(np.float64))
+    lat.step(25)
+    f = lat.get_f()
+    assert abs(f.sum() - m0) < 1e-12 * m0
+    j = np.einsum("kzyx,ka->a", f, e.astype(np.float64))
+    assert np.allclose(j, j0 + 25 * n * g, rtol=0, atol=1e-13)
+
+
+def test_rest_state_is_invariant_with_cli_walls():
+    """g = 0 and fluid at rest: every wall rule must return the rest state
+    (a w - a w + w = w for the CLI coefficients)."""
+    sp = [[5.3, 4.7, 5.1, 2.6], [1.2, 8.9, 3.3, 1.9]]
+    lat = O.Lattice(10, 10, 10, False, sp, 0.8, 3 / 16, (0.0, 0.0, 0.0), 0.3, 0.7).init()
+    lat.step(7)
+    rho, u = lat.moments()
+    fl = lat.solid() == 0
+    assert np.max(np.abs(rho[fl] - 1.0)) < 1e-14
+    assert np.max(np.abs(u)) < 1e-15
+
+
+def test_sphere_array_permeability_series():
+    """Simple-cubic array of spheres (CLI on curved walls, Sec. 2.2) against the
+    dilute-array drag series of Sangani & Acrivos; resolution-limited, the
+    deviation is 0.3% at a = 6 and falls with resolution."""
+    gs = _golden("sangani_acrivos_sc.json")
+    L, a, g = 24, 6.0, 1e-6
+    lat = O.Lattice(L, L, L, True, [[L / 2 + 0.25, L / 2 + 0.125, L / 2 + 0.375, a]], 1.0, 3 / 16,
+                    (g, 0.0, 0.0)).init()
+    lat.residual()
+    res, n = 1.0, 0
+    while res > 1e-9 and n < 20000:
+        lat.step(200)
+        n += 200
+        res = lat.residual()
+    assert res <= 1e-9
+    c = 4.0 / 3.0 * math.pi * a ** 3 / L ** 3
+    inv_k = sum(cf * c ** p for cf, p in zip(gs["coeffs"], gs["powers"]))
+    k_series = L ** 3 * inv_k / (6 * math.pi * a)   # nu <u> / g with F = g L^3
+    assert abs(lat.permeability() / k_series - 1.0) < 0.01
+
+
+# ---------------------------------------------------------------------------
+# Geometry: voxelisation, link fractions, lists, sphere placement
+# ---------------------------------------------------------------------------
+def _brute_mask(nx, ny, nz, periodic_z, spheres):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    solid = np.zeros((nz, ny, nx), bool)
+    if not periodic_z:
+        solid[0] = solid[-1] = True
+    for cx, cy, cz, r in spheres:
+        dx = np.abs(x - cx) % nx
+        dx = np.minimum(dx, nx - dx)
+        dy = np.abs(y - cy) % ny
+        dy = np.minimum(dy, ny - dy)
+        dz = np.abs(z - cz)
+        if periodic_z:
+            dz = dz % nz
+            dz = np.minimum(dz, nz - dz)
+        solid |= dx * dx + dy * dy + dz * dz <= r * r
+    return solid.astype(np.uint8)
+
+
+@pytest.mark.parametrize("periodic_z", [True, False])
+def test_voxelize_matches_enumeration(periodic_z):
+    rng = np.random.default_rng(3)
+    nx, ny, nz = 20, 17, 15
+    sp = np.column_stack([np.floor(rng.uniform(0, nx, 9) * 1024) / 1024,
+                          np.floor(rng.uniform(0, ny, 9) * 1024) / 1024,
+                          np.floor(rng.uniform(-2, nz + 2, 9) * 1024) / 1024,
+                          np.floor(rng.uniform(1.5, 4.0, 9) * 1024) / 1024])
+    sp = np.vstack([sp, [[0.0, 0.0, 3.0, 3.0], [19.5, 8.0, 7.0, 2.0]]])   # exact-grid and wrap cases
+    assert (O.voxelize(nx, ny, nz, periodic_z, sp) == _brute_mask(nx, ny, nz, periodic_z, sp)).all()
+
+
+def test_link_q_hand_cases():
+    for c in _golden("link_q_cases.json")["cases"]:
+        q = O.link_q(*c["box"], c["periodic_z"], c["spheres"], *c["node"], c["k"],
+                     q_lo=c["q_lo"], q_hi=c["q_hi"])
+        assert abs(q - c["q"]) < 1e-15, c["note"]
+
+
+def _q_bisect(node, e, spheres, box):
+    """Fraction of the link node -> node+e before the first solid point,
+    found by bisection on sampled inside/outside tests (no quadratic formula)."""
+    nx, ny, nz = box
+    p0 = np.array(node, float)
+    e = np.array(e, float)
+
+    def inside(s):
+        p = p0 + s * e
+        for cx, cy, cz, r in spheres:
+            for mx in (-1, 0, 1):
+                for my in (-1, 0, 1):
+                    for mz in (-1, 0, 1):
+                        d = p - np.array([cx + mx * nx, cy + my * ny, cz + mz * nz])
+                        if d @ d <= r * r:
+                            return True
+        return False
+
+    # first crossing: march then bisect
+    s_prev = 0.0
+    for s in np.linspace(0, 1, 257)[1:]:
+        if inside(s):
+            lo, hi = s_prev, s
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                lo, hi = (lo, mid) if inside(mid) else (mid, hi)
+            return hi
+        s_prev = s
+    return None
+
+
+def test_link_q_against_bisection():
+    rng = np.random.default_rng(11)
+    box = (14, 13, 12)
+    sp, _, rc = O.place_spheres(*box, True, 0.0, 12.0, 1.5, 3.5, 0.75, True, 99)
+    assert rc == 0 and len(sp) > 3
+    lists = O.build_lists(*box, True, sp)
+    e, _ = O.velocity_set()
+    fluid = lists["fluid_cell"]
+    picks = rng.choice(len(lists["link_k"]), size=60, replace=False)
+    for li in picks:
+        c = int(fluid[lists["link_cell"][li]])
+        k = int(lists["link_k"][li])
+        node = (c % box[0], (c // box[0]) % box[1], c // (box[0] * box[1]))
+        qb = _q_bisect(node, e[k], sp, box)
+        assert qb is not None
+        assert abs(qb - lists["link_q"][li]) < 1e-12
+
+
+def test_lists_are_consistent():
+    nx, ny, nz = 16, 12, 14
+    sp, _, rc = O.place_spheres(nx, ny, nz, False, 1.0, 7.0, 2.0, 3.0, 0.7, False, 5)
+    assert rc == 0
+    L = O.build_lists(nx, ny, nz, False, sp, q_lo=0.25, q_hi=0.5)
+    mask = O.voxelize(nx, ny, nz, False, sp).reshape(-1)
+    fluid = L["fluid_cell"]
+    assert (fluid == np.flatnonzero(mask == 0)).all()
+    e, _ = O.velocity_set()
+    nbr = L["nbr"]
+    nf = len(fluid)
+    x, y, z = fluid % nx, (fluid // nx) % ny, fluid // (nx * ny)
+    for k in range(1, 19):
+        xn, yn, zn = (x + e[k, 0]) % nx, (y + e[k, 1]) % ny, z + e[k, 2]
+        inb = (zn >= 0) & (zn < nz)
+        cn = xn + nx * (yn + ny * np.clip(zn, 0, nz - 1))
+        want = np.where(inb & (mask[cn] == 0), np.searchsorted(fluid, cn), -1)
+        assert (nbr[k - 1] == want).all()
+        kb = O.opposite(k)
+        ok = nbr[k - 1] >= 0
+        assert (nbr[kb - 1][nbr[k - 1][ok]] == np.arange(nf)[ok]).all()
+    # links are exactly the (cell, k) with a solid neighbour, in (cell, k) order
+    lc, lk = L["link_cell"], L["link_k"]
+    want = [(i, k) for i in range(nf) for k in range(1, 19) if nbr[k - 1][i] < 0]
+    assert list(zip(lc.tolist(), lk.tolist())) == want
+    assert ((L["link_q"] > 0) & (L["link_q"] <= 1)).all()
+    fb = np.array([nbr[O.opposite(k) - 1][i] < 0 for i, k in want])
+    assert (L["link_fallback"].astype(bool) == fb).all()
+    # links into the bottom wall layer from z = 1 that no sphere reaches carry q_lo
+    zl = z[lc]
+    wall = (zl == 1) & (e[lk, 2] == -1)
+    assert np.all(L["link_q"][wall] <= 0.25) and np.any(L["link_q"][wall] == 0.25)
+
+
+def test_place_spheres_rules():
+    nx, ny, nz = 32, 32, 64
+    sp, phi, rc = O.place_spheres(nx, ny, nz, False, 1.0, 32.0, 4.0, 4.0, 0.7, False, 1)
+    assert rc == 0
+    # quantised, inside the ranges
+    assert np.all(sp * 1024 == np.floor(sp * 1024))
+    assert np.all((sp[:, 0] >= 0) & (sp[:, 0] < nx) & (sp[:, 2] >= 1) & (sp[:, 2] < 32))
+    assert np.all(sp[:, 3] == 4.0)
+    # no overlap under minimum image in x, y
+    for i in range(len(sp)):
+        d = sp[i, :3] - sp[:i, :3]
+        d[:, :2] -= np.round(d[:, :2] / [nx, ny]) * [nx, ny]
+        assert np.all((d * d).sum(1) >= (2 * 4.0) ** 2)
+    # the stop rule: porosity of the layer z = 1..31 drops to the target with
+    # the last sphere and not before
+    def layer_phi(s):
+        m = _brute_mask(nx, ny, nz, False, s)
+        return 1.0 - m[1:32].mean()
+    assert abs(layer_phi(sp) - phi) < 1e-15 and phi <= 0.7
+    assert layer_phi(sp[:-1]) > 0.7
+    # deterministic for the seed
+    sp2, _, _ = O.place_spheres(nx, ny, nz, False, 1.0, 32.0, 4.0, 4.0, 0.7, False, 1)
+    assert (sp2 == sp).all()
+
+
+def test_place_spheres_unreachable_packing():
+    """Non-overlapping monodisperse spheres cannot fill 90% of a layer."""
+    _, _, rc = O.place_spheres(24, 24, 24, True, 0.0, 24.0, 4.0, 4.0, 0.1, False, 3,
+                               max_rejects=2000)
+    assert rc == -2
+
+
+def test_plane_average_definitions():
+    nx, ny, nz = 8, 6, 10
+    sp = [[4.0, 3.0, 4.0, 2.0]]
+    g = (2e-6, 0.0, 0.0)
+    lat = O.Lattice(nx, ny, nz, False, sp, 0.8, 3 / 16, g)
+    rng = np.random.default_rng(2)
+    u0 = 1e-3 * rng.standard_normal((3, nz, ny, nx))
+    lat.init(u0)
+    pa = lat.plane_average()
+    solid = lat.solid().astype(bool)
+    ux = np.where(solid, 0.0, u0[0] + g[0] / 2)    # j = u0 right after init
+    nfl = (~solid).sum(axis=(1, 2))
+    assert np.allclose(pa[:, 0], ux.sum(axis=(1, 2)) / (nx * ny), rtol=0, atol=1e-15)
+    intr = np.where(nfl > 0, ux.sum(axis=(1, 2)) / np.maximum(nfl, 1), 0.0)
+    assert np.allclose(pa[:, 1], intr, rtol=0, atol=1e-15)
+    assert np.allclose(pa[:, 2], nfl / (nx * ny), rtol=0, atol=0)
+    assert pa[0, 2] == 0 and pa[-1, 2] == 0
+
+
+def test_residual_definition():
+    lat = O.Lattice(4, 4, 8, False, (), 0.8, 3 / 16, (1e-6, 0, 0)).init()
+    assert math.isinf(lat.residual())
+    _, u1 = lat.moments()
+    lat.step(10)
+    _, u2 = lat.moments()
+    r = lat.residual()
+    assert abs(r - np.linalg.norm(u2 - u1) / np.linalg.norm(u2)) < 1e-14
+
+
+def test_binned_link_search_equals_exhaustive():
+    """The bin pruning used for large boxes returns the same q bit for bit."""
+    box = (40, 36, 30)
+    sp, _, rc = O.place_spheres(*box, False, 1.0, 20.0, 2.0, 5.0, 0.5, True, 17)
+    assert rc == 0
+    a = O.build_lists(*box, False, sp, q_lo=0.4, q_hi=0.6)
+    b = O.build_lists(*box, False, sp, q_lo=0.4, q_hi=0.6, use_bins=True)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
