@@ -1,0 +1,307 @@
+"""Throughput of the fused D3Q19 TRT + CLI step (fluid MLUPS and HBM roofline).
+
+Workload: the 256x256x512 channel with a porous layer z < 256 of r = 8 sphere
+packings at porosities {0.4, 0.6, 0.8, 0.9} (one solver per porosity, FP32
+storage); one bench step = one lattice time step of all four solvers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+only other program here; see the "cpu_baseline" key).  Multi-GPU runs are
+independent replicas (one process per GPU, no data exchange): the LBM of one
+box runs on one GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1507_06565_gb300 import workloads as W  # noqa: E402
+
+STORED_BYTES_F32 = 19 * 2 * 4   # algorithmic bytes per fluid lattice update (19 reads + 19 writes)
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "fluid MLUPS (D3Q19 TRT + CLI stream-collide, % of HBM roofline in 'roofline')"
+WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlapping r=8 spheres, "
+            "porosity sweep {0.4,0.6,0.8,0.9} (one solver each); one step = one time step of all four")
+# bounded samples of the workload for the CPU oracle: same sphere radius,
+# porosity and channel structure at a reduced box
+SAMPLE = W.Channel("W2-shaped sample 128x128x256 r=8 phi=0.6", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, 0.6, True, 2060)
+SAMPLE_STEP = W.Channel("W2-shaped sample 64x64x128 r=8 phi=0.6", 64, 64, 128, 1.0, 64.0, 8.0, 8.0, 0.6, True, 2060)
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peak_hbm():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(steps: int, warmup: int):
+    """FP64 oracle on the host cores over the small W2-shaped sample channel."""
+    import oracle as O
+
+    sp, _, rc = O.place_spheres(*SAMPLE_STEP.sphere_args())
+    assert rc == 0
+    lat = O.Lattice(SAMPLE_STEP.nx, SAMPLE_STEP.ny, SAMPLE_STEP.nz, False, sp, SAMPLE_STEP.tau, SAMPLE_STEP.lam,
+                    SAMPLE_STEP.g).init()
+    nf = int((lat.solid() == 0).sum())
+    lat.step(warmup)
+    t0 = time.perf_counter()
+    lat.step(steps)
+    dt = time.perf_counter() - t0
+    return nf, dt, O.threads()
+
+
+def cpu_baseline(seconds_hint: float = 15.0):
+    import oracle as O
+
+    sp, _, _ = O.place_spheres(*SAMPLE.sphere_args())
+    lat = O.Lattice(SAMPLE.nx, SAMPLE.ny, SAMPLE.nz, False, sp, SAMPLE.tau, SAMPLE.lam, SAMPLE.g).init()
+    nf = int((lat.solid() == 0).sum())
+    t0 = time.perf_counter()
+    lat.step(1)
+    one = time.perf_counter() - t0
+    n = max(2, min(200, int(seconds_hint / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    lat.step(n)
+    dt = time.perf_counter() - t0
+    return {"value": nf * n / dt / 1e6, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
+            "sample": f"{SAMPLE.name} ({nf} fluid cells), FP64 dense two-array oracle, {n} steps after 1 warm-up"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    nf, dt, cores = _oracle_sample(args.steps, args.warmup)
+    value = nf * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": SAMPLE_STEP.name, "fluid_cells": nf},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{SAMPLE_STEP.name}: one oracle time step per bench step"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    L.load_library()
+    stream = torch.cuda.current_stream()
+
+    if args.workload == "channel":
+        cases = [W.W2(phi) for phi in W.W2_POROSITIES]
+    else:   # the same channel at half the size in each direction, for profiler captures
+        cases = [W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True,
+                           W.W2(phi).seed) for phi in W.W2_POROSITIES]
+    geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
+    solvers = [L.Solver(g, c.tau, c.lam, c.g, "f32") for g, c in zip(geoms, cases)]
+    nfs = [s.info()["n_fluid"] for s in solvers]
+    nf_total = sum(nfs)
+    lib = L.load_library()
+
+    def one_step(events=None):
+        for s in solvers:
+            if events is not None:
+                events[0].append(torch.cuda.Event(enable_timing=True))
+                events[1].append(torch.cuda.Event(enable_timing=True))
+                events[0][-1].record(stream)
+            rc = lib.lbm_step(s.handle, 1)
+            if rc:
+                raise L.LBMError(rc, "lbm_step")
+            if events is not None:
+                events[1][-1].record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = ([], [])
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        one_step(ev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    durs = np.array([a.elapsed_time(b) for a, b in zip(*ev)]).reshape(args.steps, len(solvers))
+    first_parity = args.warmup & 1   # parity of the first timed step
+    # per-launch algorithmic bytes: 152 B per fluid cell (19 loads + 19 stores of FP32)
+    bytes_per_launch = np.array(nfs, dtype=np.float64) * STORED_BYTES_F32
+    achieved = float((bytes_per_launch[None, :] / (durs * 1e-3)).mean() / 1e9)
+    parity = {}
+    for off in (0, 1):
+        sel = durs[off::2]
+        if sel.size:
+            name = "even" if (first_parity + off) % 2 == 0 else "odd"
+            parity[name] = float((bytes_per_launch[None, :] / (sel * 1e-3)).mean() / 1e9)
+    peak, peak_kind = _peak_hbm()
+    value = nf_total * args.steps * world / (ms * 1e-3) / 1e6
+
+    # end to end through the public API with host buffers: lbm_init from the
+    # host geometry (mask and sphere bins copied host->device), E2E_STEPS
+    # steps, plane averages copied back to the host
+    e2e_steps = max(10, args.steps // 4)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    h2d = 0
+    d2h = 0
+    for g, c in zip(geoms, cases):
+        s2 = L.Solver(g, c.tau, c.lam, c.g, "f32")
+        s2.step(e2e_steps)
+        pa = s2.plane_average()
+        h2d += g.mask().nbytes
+        d2h += pa.nbytes
+        del s2
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    e2e_value = nf_total * e2e_steps / e2e_s / 1e6
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "channel" else WORKLOAD.replace("256x256x512", "128x128x256"),
+                   "fluid_cells": nfs, "storage": "f32",
+                   "l2": "inputs larger than L2 (4.1-5.7 GB of populations and indices per solver)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_step_even/k_step_odd (fused AA stream-collide + CLI)",
+                     "bytes_per_flup": STORED_BYTES_F32, "peak_kind": peak_kind, "by_parity": parity},
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps,
+                "what": f"lbm_init from host geometry + {e2e_steps} steps + plane averages to host, all four solvers"},
+        "clocks": clk,
+        "gpu_launches": args.steps * len(solvers),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["channel", "channel-half"], default="channel",
+                    help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for profiling")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * lbm.h -- C ABI of the GB300 pore-scale lattice Boltzmann library (liblbm.so).
+ *
+ * Method: Fattahi, Waluga, Wohlmuth & Ruede, "Large scale lattice Boltzmann
+ * simulation for the coupling of free and porous media flow".  A D3Q19
+ * two-relaxation-time scheme (Sec. 2.1, Eqs. (LBM), (TRT), (TRT2),
+ * (equilibrium), (Macro), (collision), (streaming)) driven by a body force,
+ * with central-linear-interpolation bounce-back on every wall link
+ * (Sec. 2.2, Eq. (CLI); q = 1/2 is simple bounce-back, Eq. (noslip)), on
+ * voxelised sphere packings (Sec. 3.1), with plane averages of the stream-wise
+ * velocity (Sec. 3.1) and the Darcy permeability (Eq. (Darcy)).
+ *
+ * Conventions shared by every call:
+ *  - Return value: LBM_OK (0) on success, a negative LBM_E* code on failure.
+ *    No C++ exception crosses the ABI.  lbm_status_string() names a code.
+ *  - Geometry and solver handles are owned by the library and freed by their
+ *    *_destroy call.  All device memory is owned by the caller: the solver
+ *    lives in one caller-allocated device workspace of lbm_workspace_size()
+ *    bytes (256-byte aligned) that must outlive the solver.
+ *  - Streams: lbm_init() binds the solver to a CUDA stream (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream).  Device-side calls are
+ *    asynchronous on that stream; calls that return host values synchronise
+ *    that stream only.
+ *  - Layouts: dense fields are [nz][ny][nx] with x fastest (cell index
+ *    c = x + nx (y + ny z)); vectors are component-major [3][nz][ny][nx].
+ *    Fluid cells are numbered 0..n_fluid-1 in increasing cell index.
+ *  - D3Q19 ordering: k = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),
+ *    (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1),
+ *    (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1); the opposite of k >= 1 is k+1
+ *    for odd k and k-1 for even k.
+ *  - Lattice units throughout (dx = dt = 1, rho0 = 1).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)       /* bad argument (NULL handle, size out of range, ...) */
+#define LBM_ENOMEM (-2)       /* host allocation failed */
+#define LBM_ECUDA (-3)        /* a CUDA runtime call failed */
+#define LBM_EPACKING (-4)     /* target porosity unreachable without overlap */
+#define LBM_ENAN (-5)         /* a NaN or Inf appeared in the velocity field */
+#define LBM_ENOTCONVERGED (-6)/* lbm_run_until reached max_steps */
+#define LBM_ETIMEOUT (-7)     /* a bounded device-side wait gave up */
+#define LBM_ESIZE (-8)        /* workspace too small or misaligned */
+
+/* ---- storage precision of the populations ---- */
+#define LBM_F32 0
+#define LBM_F16 1
+#define LBM_BF16 2
+
+typedef struct lbm_geometry lbm_geometry;
+typedef struct lbm_solver lbm_solver;
+
+/* Box.  x and y are always periodic.  With periodic_z == 0 the cell layers
+ * z = 0 and z = nz-1 are solid no-slip walls (Sec. 3.1: walls at top and
+ * bottom, periodic stream- and span-wise); their surfaces lie at the link
+ * fractions q_lo and q_hi from the adjacent fluid nodes (1/2 = half-way,
+ * Eq. (noslip)).  Limits: 1 <= nx, ny, nz and nx*ny*nz < 2^31. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t periodic_z;
+    double q_lo, q_hi;
+} lbm_box;
+
+/* Seeded sphere placement standing in for the settled rigid-body packing of
+ * Sec. 3.1 (the paper's particle code is not available).  Candidates draw, in
+ * order, x in [0,nx), y in [0,ny), z in [layer_z0, layer_z1) and r in
+ * [r_min, r_max) from SplitMix64 (Steele, Lea & Flood 2014) seeded with
+ * `seed`, each value u = (next >> 11) 2^-53 scaled and rounded down to the
+ * 2^-10 grid.  With allow_overlap == 0 a candidate closer than the radius sum
+ * (minimum image) to an earlier sphere is rejected, and max_rejects
+ * consecutive rejections give LBM_EPACKING.  Spheres are added until the voxel
+ * porosity of the cells with ceil(layer_z0) <= z < ceil(layer_z1) (wall layers
+ * excluded) is <= porosity; more than max_spheres gives LBM_EINVAL.
+ * Requires 2 r_max < nx, ny (and nz when periodic). */
+typedef struct {
+    lbm_box box;
+    double layer_z0, layer_z1;
+    double r_min, r_max;
+    double porosity;
+    int32_t allow_overlap;
+    uint64_t seed;
+    int64_t max_spheres;
+    int64_t max_rejects;
+} lbm_sphere_params;
+
+/* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
+ * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes
+ * omega- (Sec. 2.1; 3/16 puts bounce-back walls exactly half-way).  g is the
+ * body force per unit mass (the source F_k = 3 w_k e_k.g of Eq. (collision)).
+ * storage is LBM_F32, LBM_F16 or LBM_BF16. */
+typedef struct {
+    double tau;
+    double lambda;
+    double g[3];
+    int32_t storage;
+    int32_t reserved;
+} lbm_params;
+
+typedef struct {
+    int64_t n_cells;   /* nx*ny*nz */
+    int64_t n_fluid;   /* fluid cells */
+    int64_t n_links;   /* wall links (fluid cell, k) with a solid neighbour */
+    int64_t n_spheres;
+    double porosity;   /* voxel porosity of the placement layer (placement) or of the box */
+} lbm_geometry_info;
+
+/* ------------------------------------------------------------------------- */
+/* Geometry (host side; the library owns the handle).                        */
+/* ------------------------------------------------------------------------- */
+
+/* Place spheres (see lbm_sphere_params) and voxelise them: a cell (integer
+ * centre) is solid if it is a wall layer or lies within distance r of any
+ * periodic image of a sphere.  *out receives a new handle.
+ * Errors: LBM_EINVAL, LBM_EPACKING, LBM_ENOMEM. */
+int lbm_geometry_from_spheres(const lbm_sphere_params *params, lbm_geometry **out);
+
+/* Same from an explicit sphere list xyzr[n][4] = (x, y, z, r), copied.
+ * Centres may lie outside the box (e.g. below the bottom wall, Sec. 3.1).
+ * Errors: LBM_EINVAL (r <= 0, 2r >= a periodic extent), LBM_ENOMEM. */
+int lbm_geometry_from_list(const lbm_box *box, const double *xyzr, int64_t n, lbm_geometry **out);
+
+/* Counts of a geometry. */
+int lbm_geometry_info_get(const lbm_geometry *geom, lbm_geometry_info *out);
+
+/* Copy the sphere list into host xyzr[cap][4]; *n receives the count.
+ * LBM_ESIZE if cap is too small. */
+int lbm_geometry_spheres(const lbm_geometry *geom, double *xyzr, int64_t cap, int64_t *n);
+
+/* Copy the solid mask (1 = solid) into host mask[nz][ny][nx]. */
+int lbm_geometry_mask(const lbm_geometry *geom, uint8_t *mask);
+
+void lbm_geometry_destroy(lbm_geometry *geom);
+
+/* ------------------------------------------------------------------------- */
+/* Solver (device side).                                                      */
+/* ------------------------------------------------------------------------- */
+
+/* Bytes of device workspace lbm_init needs for this geometry and params. */
+int lbm_workspace_size(const lbm_geometry *geom, const lbm_params *params, size_t *bytes);
+
+/* Build the device fluid list, neighbour table and wall-link list (with q) in
+ * the caller's workspace, then initialise the populations to the equilibrium
+ * f_k^eq(rho = 1, u0) of Eq. (equilibrium).  dev_u0 is a device velocity
+ * field [3][nz][ny][nx] (float) or NULL for rest.  stream is a cudaStream_t
+ * (NULL = default stream); the call returns after the set-up has completed on
+ * it.  The workspace must be 256-byte aligned and at least
+ * lbm_workspace_size() bytes (else LBM_ESIZE).  The geometry may be destroyed
+ * after this call.  Errors: LBM_EINVAL, LBM_ESIZE, LBM_ECUDA, LBM_ENOMEM. */
+int lbm_init(const lbm_geometry *geom, const lbm_params *params, void *dev_workspace, size_t bytes,
+             const float *dev_u0, void *stream, lbm_solver **out);
+
+/* Re-initialise the populations of an existing solver (step count back to 0)
+ * from dev_u0 (or rest when NULL). */
+int lbm_reset(lbm_solver *solver, const float *dev_u0);
+
+/* Advance n >= 0 time steps (collision, Eq. (collision), then streaming,
+ * Eq. (streaming), with Eq. (CLI) on every wall link), asynchronously on the
+ * solver's stream. */
+int lbm_step(lbm_solver *solver, int64_t n);
+
+/* Moments of the current state (Eq. (Macro)): rho = sum_k f_k and the velocity
+ * u = j + g/2 (j = sum_k e_k f_k, rho0 = 1; g/2 makes u the mean of the pre-
+ * and post-collision momentum).  Dense device outputs dev_rho[nz][ny][nx] and
+ * dev_u[3][nz][ny][nx] (float; either may be NULL); solid cells get 0.
+ * Asynchronous on the solver's stream. */
+int lbm_moments(lbm_solver *solver, float *dev_rho, float *dev_u);
+
+/* Plane averages of the stream-wise velocity (Sec. 3.1), summed in FP64 on the
+ * device: host_out[nz][3] = (sum_fluid u_x / (nx ny), sum_fluid u_x / n_fluid(z)
+ * or 0 for an all-solid plane, n_fluid(z) / (nx ny)).  Synchronises the
+ * stream. */
+int lbm_plane_average(lbm_solver *solver, double *host_out);
+
+/* Darcy permeability along x (Eq. (Darcy) with mu = rho0 nu, no mean pressure
+ * gradient and the body force g_x): K = nu <u_x> / g_x with <u_x> the
+ * superficial mean over the planes z_lo..z_hi (both -1: the whole box),
+ * reduced in FP64 on the device.  Synchronises the stream.  LBM_EINVAL if
+ * g_x == 0 or the window is out of range. */
+int lbm_permeability(lbm_solver *solver, int32_t z_lo, int32_t z_hi, double *k_out);
+
+/* Convergence residual ||u - u_prev||_2 / ||u||_2 over all fluid cells and
+ * components (FP64 sums on the device), where u_prev is the velocity at the
+ * previous call; the first call after lbm_init/lbm_reset returns +inf.
+ * Synchronises the stream.  LBM_ENAN if the field holds a NaN or Inf. */
+int lbm_residual(lbm_solver *solver, double *res_out);
+
+/* Convergence residual of the plane-averaged stream-wise velocity (the
+ * quantity Sec. 3.1 reports at steady state): ||P - P_prev||_2 / ||P||_2 over
+ * the nz superficial plane averages P(z) of lbm_plane_average, against the
+ * profile at the previous call (+inf on the first call after
+ * lbm_init/lbm_reset).  Unlike the field residual it is not limited by the
+ * slow drift of the local velocity that the mass imbalance of Eq. (CLI)
+ * causes, nor by storage round-off.  Synchronises the stream.  LBM_ENAN on a
+ * non-finite profile. */
+int lbm_profile_residual(lbm_solver *solver, double *res_out);
+
+/* Mean density deviation <rho - 1> over the fluid cells (FP64 sum on the
+ * device).  The CLI rule (Eq. (CLI)) does not conserve mass exactly, so in a
+ * steady flow this drifts linearly in time.  Synchronises the stream. */
+int lbm_mass(lbm_solver *solver, double *mean_drho);
+
+/* Remove the mean density deviation: the next lbm_step subtracts
+ * w_k <rho - 1> from every population before its collision.  The scheme is
+ * invariant under such a uniform shift (the TRT split, the source term and
+ * Eq. (CLI), a w - a w + w = w, all commute with it), so velocities are
+ * unchanged in exact arithmetic; it keeps the stored populations small so
+ * that reduced-precision storage keeps its resolution in long runs.
+ * *shift_out (may be NULL) receives the scheduled shift.  Synchronises the
+ * stream. */
+int lbm_recenter(lbm_solver *solver, double *shift_out);
+
+#define LBM_CONVERGE_FIELD 0    /* lbm_residual */
+#define LBM_CONVERGE_PROFILE 1  /* lbm_profile_residual */
+
+/* Step in chunks of `interval` until the residual selected by `criterion`
+ * (LBM_CONVERGE_FIELD or LBM_CONVERGE_PROFILE) is below tol, taking at least
+ * one chunk; the density is re-centred (lbm_recenter) after every chunk.  *steps_done and *res_out receive the steps taken and the last
+ * residual.  LBM_ENOTCONVERGED after max_steps, LBM_ENAN on divergence. */
+int lbm_run_until(lbm_solver *solver, double tol, int64_t interval, int64_t max_steps, int32_t criterion,
+                  int64_t *steps_done, double *res_out);
+
+/* Steps taken since lbm_init/lbm_reset. */
+int lbm_steps_done(const lbm_solver *solver, int64_t *steps);
+
+/* Counts of the solver's device lists. */
+int lbm_solver_info(const lbm_solver *solver, lbm_geometry_info *out);
+
+/* Copy the device lists to host buffers (any may be NULL):
+ * fluid_cell[n_fluid] cell index of each fluid cell; nbr[18][n_fluid] fluid
+ * index of the neighbour along e_k (k = 1..18) or -1 when solid;
+ * link_cell/link_k/link_q/link_fallback[n_links]: one record per wall link in
+ * (cell, k) order with the link fraction q of Eq. (CLI) and 1 when the second
+ * fluid node x_f1 - e_k is solid (the link then uses bounce-back, a = 0).
+ * Synchronises the stream. */
+int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int32_t *link_cell,
+                     int8_t *link_k, double *link_q, uint8_t *link_fallback);
+
+/* Shifted populations h_k = f_k - w_k of the current state (the streamed
+ * populations of Eq. (streaming) at the current time) into the device buffer
+ * dev_out[19][n_fluid] (float).  Asynchronous. */
+int lbm_populations(lbm_solver *solver, float *dev_out);
+
+void lbm_solver_destroy(lbm_solver *solver);
+
+const char *lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,278 @@
+// lbm_build.cu -- device construction of the sparse fluid list, the neighbour
+// table and the wall-link list with the link fractions q of Eq. (CLI).
+//
+// Steps (all on the solver's stream):
+//   1. per block of cells: count fluid cells of the uploaded solid mask;
+//      exclusive scan of the block counts;
+//   2. dense index map cell -> fluid index (-1 solid) and fluid_cell[];
+//   3. neighbour table nbr[k][i] and link mask lmask[i] (bit k: x + e_k solid),
+//      link counts per aligned group of 32 fluid cells; exclusive scan;
+//   4. link fraction q and CLI coefficient a = (1-2q)/(1+2q) per link
+//      (a = 0, bounce-back, when the second node x - e_k is solid);
+//   5. first fluid index of each z plane.
+// The index map and the mask live in the population region, which is written
+// only afterwards by the initialisation.
+#include <cstdio>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// 1. fluid count per block of kBlock cells
+__global__ void k_count_fluid(const uint8_t *__restrict__ mask, int64_t ncell, uint32_t *__restrict__ counts)
+{
+    const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int fluid = c < ncell && !mask[c];
+    const int n = __syncthreads_count(fluid);
+    if (threadIdx.x == 0) counts[blockIdx.x] = (uint32_t)n;
+}
+
+// Exclusive scan of n uint32 values in place by one block; the total goes to
+// *total.  Sequential over chunks of kScanThreads with a running carry.
+__global__ void k_scan_exclusive(uint32_t *__restrict__ v, int64_t n, uint32_t *__restrict__ total)
+{
+    __shared__ uint32_t warp_sums[kScanThreads / 32];
+    __shared__ uint32_t carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < n; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t x = i < n ? v[i] : 0u;
+        uint32_t s = x;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        if (lane == 31) warp_sums[warp] = s;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = warp_sums[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            warp_sums[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t carry = carry_s;
+        const uint32_t before = (warp ? warp_sums[warp - 1] : 0u) + s - x;
+        if (i < n) v[i] = carry + before;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry_s = carry + warp_sums[kScanThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry_s;
+}
+
+// 2. index map and fluid list (fluid cells keep increasing cell order)
+__global__ void k_fill_index(const uint8_t *__restrict__ mask, int64_t ncell,
+                             const uint32_t *__restrict__ block_off, int32_t *__restrict__ idx_map,
+                             int32_t *__restrict__ fluid_cell)
+{
+    __shared__ uint32_t warp_cnt[kBlock / 32];
+    const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const bool fluid = c < ncell && !mask[c];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ballot = __ballot_sync(0xffffffffu, fluid);
+    if (lane == 0) warp_cnt[warp] = __popc(ballot);
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_cnt[w];
+    before += __popc(ballot & ((1u << lane) - 1u));
+    if (c < ncell) {
+        const int32_t idx = fluid ? (int32_t)(block_off[blockIdx.x] + before) : -1;
+        idx_map[c] = idx;
+        if (fluid) fluid_cell[idx] = (int32_t)c;
+    }
+}
+
+// 3. neighbour table, link mask, link count per aligned group of 32 cells
+__global__ void k_neighbours(const int32_t *__restrict__ idx_map, const int32_t *__restrict__ fluid_cell,
+                             int32_t n_fluid, int32_t n_pad, int nx, int ny, int nz, int periodic_z,
+                             int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
+                             uint32_t *__restrict__ warp_cnt)
+{
+    const int32_t i = blockIdx.x * kBlock + threadIdx.x;
+    uint32_t m = 0;
+    if (i < n_fluid) {
+        const int32_t c = fluid_cell[i];
+        const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+#pragma unroll
+        for (int k = 1; k < kQ; ++k) {
+            const int xn = wrap(x + ex(k), nx), yn = wrap(y + ey(k), ny);
+            int zn = z + ez(k);
+            int32_t j = -1;
+            if (periodic_z) zn = wrap(zn, nz);
+            if (zn >= 0 && zn < nz) j = idx_map[xn + nx * (yn + ny * zn)];
+            nbr[(size_t)(k - 1) * n_pad + i] = j;
+            m |= (uint32_t)(j < 0) << k;
+        }
+    } else if (i < n_pad) {
+        for (int k = 1; k < kQ; ++k) nbr[(size_t)(k - 1) * n_pad + i] = -1;
+    }
+    if (i < n_pad) lmask[i] = m;
+    uint32_t cnt = __popc(m);
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    if ((threadIdx.x & 31) == 0) warp_cnt[i >> 5] = cnt;
+}
+
+// Entry parameter s in (0,1] of the ray p + s e into the sphere |x - c| <= r,
+// d = p - c, p outside.  2.0 when the ray does not enter within the link.
+// Every product and sum here is exact for coordinates on the 2^-10 grid; the
+// explicit round-to-nearest intrinsics keep the compiler from contracting.
+__device__ double sphere_entry(double dx, double dy, double dz, int kx, int ky, int kz, double r)
+{
+    const double A = (double)(kx * kx + ky * ky + kz * kz);
+    const double B = __dadd_rn(__dadd_rn(__dmul_rn(dx, (double)kx), __dmul_rn(dy, (double)ky)),
+                               __dmul_rn(dz, (double)kz));
+    const double C = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)),
+                               __dmul_rn(r, r));
+    const double disc = __dsub_rn(__dmul_rn(B, B), __dmul_rn(A, C));
+    if (!(B < 0.0) || disc < 0.0) return 2.0;
+    const double s = __ddiv_rn(__dsub_rn(-B, __dsqrt_rn(disc)), A);
+    return s <= 1.0 ? s : 2.0;
+}
+
+struct LinkArgs {
+    const int32_t *fluid_cell;
+    const uint32_t *lmask;
+    const uint32_t *warp_off;
+    const int32_t *bin_start;
+    const SphereImage *images;
+    float *link_a;
+    double *link_q;
+    int32_t n_fluid;
+    int nx, ny, nz, periodic_z;
+    int nbx, nby;
+    double q_lo, q_hi;
+};
+
+// 4. link fractions and CLI coefficients
+__global__ void k_links(LinkArgs a)
+{
+    const int32_t i = blockIdx.x * kBlock + threadIdx.x;
+    const uint32_t m = i < a.n_fluid ? a.lmask[i] : 0u;
+    const uint32_t cnt = __popc(m);
+    uint32_t incl = cnt;
+    const int lane = threadIdx.x & 31;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (i >= a.n_fluid || m == 0) return;
+    uint32_t off = a.warp_off[i >> 5] + incl - cnt;
+    const int32_t c = a.fluid_cell[i];
+    const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+    const int bin = x / kBinEdge + a.nbx * (y / kBinEdge + a.nby * (z / kBinEdge));
+    const int b0 = a.bin_start[bin], b1 = a.bin_start[bin + 1];
+    for (int k = 1; k < kQ; ++k) {
+        if (!((m >> k) & 1u)) continue;
+        const int kx = ex(k), ky = ey(k), kz = ez(k);
+        double q = 2.0;
+        if (!a.periodic_z) {
+            const int bz = z + kz;
+            if (bz <= 0) q = a.q_lo;
+            if (bz >= a.nz - 1 && a.q_hi < q) q = a.q_hi;
+        }
+        for (int b = b0; b < b1; ++b) {
+            const SphereImage im = a.images[b];
+            // A link of length <= sqrt(2) can only enter a sphere whose centre is
+            // within r + sqrt(2) of its start; the FP32 test keeps a margin of
+            // ~0.17 r over that bound, so it never drops a candidate.
+            const float fx = (float)x - (float)im.x, fy = (float)y - (float)im.y, fz = (float)z - (float)im.z;
+            const float reach = (float)im.r + 1.5f;
+            if (fx * fx + fy * fy + fz * fz > reach * reach) continue;
+            const double s = sphere_entry((double)x - im.x, (double)y - im.y, (double)z - im.z, kx, ky, kz, im.r);
+            if (s < q) q = s;
+        }
+        const bool fallback = (m >> opp(k)) & 1u;
+        const double coef = fallback ? 0.0 : __ddiv_rn(__dsub_rn(1.0, __dmul_rn(2.0, q)), __dadd_rn(1.0, __dmul_rn(2.0, q)));
+        a.link_q[off] = q;
+        a.link_a[off] = (float)coef;
+        ++off;
+    }
+}
+
+// 5. first fluid index of each z plane (plane_off[nz] = n_fluid)
+__global__ void k_plane_offsets(const int32_t *__restrict__ fluid_cell, int32_t n_fluid, int plane, int nz,
+                                int32_t *__restrict__ plane_off)
+{
+    const int32_t i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n_fluid) return;
+    const int z = fluid_cell[i] / plane;
+    const int zp = i == 0 ? -1 : fluid_cell[i - 1] / plane;
+    for (int zz = zp + 1; zz <= z; ++zz) plane_off[zz] = i;
+    if (i == n_fluid - 1)
+        for (int zz = z + 1; zz <= nz; ++zz) plane_off[zz] = n_fluid;
+}
+
+}  // namespace
+
+#define LBM_CUDA_TRY(x)                                     \
+    do {                                                    \
+        if ((x) != cudaSuccess) return LBM_ECUDA;           \
+    } while (0)
+
+int device_build(Solver &s, const Geometry &g, const Bins &bins)
+{
+    const Layout &L = s.lay;
+    cudaStream_t st = s.stream;
+    const int64_t ncell = s.n_cells;
+    const int nx = s.box.nx, ny = s.box.ny, nz = s.box.nz;
+    uint8_t *d_mask = (uint8_t *)(s.ws + L.mask);
+    int32_t *d_idx = (int32_t *)(s.ws + L.idx_map);
+    uint32_t *d_scan = (uint32_t *)(s.ws + L.scan_tmp);
+    uint32_t *d_wcnt = (uint32_t *)(s.ws + L.warp_cnt);
+    uint32_t *d_total = (uint32_t *)(s.ws + L.result);
+    int32_t *d_bstart = (int32_t *)(s.ws + L.bins_start);
+    SphereImage *d_img = (SphereImage *)(s.ws + L.bins_img);
+
+    LBM_CUDA_TRY(cudaMemcpyAsync(d_mask, g.mask.data(), (size_t)ncell, cudaMemcpyHostToDevice, st));
+    LBM_CUDA_TRY(cudaMemcpyAsync(d_bstart, bins.start.data(), bins.start.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, st));
+    if (!bins.images.empty())
+        LBM_CUDA_TRY(cudaMemcpyAsync(d_img, bins.images.data(), bins.images.size() * sizeof(SphereImage),
+                                     cudaMemcpyHostToDevice, st));
+
+    const int64_t nblk = (ncell + kBlock - 1) / kBlock;
+    k_count_fluid<<<(unsigned)nblk, kBlock, 0, st>>>(d_mask, ncell, d_scan);
+    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(d_scan, nblk, d_total);
+    k_fill_index<<<(unsigned)nblk, kBlock, 0, st>>>(d_mask, ncell, d_scan, d_idx, s.fluid_cell);
+    LBM_CUDA_TRY(cudaGetLastError());
+
+    const unsigned fblk = (unsigned)(s.n_pad / kBlock);
+    if (s.n_pad > s.n_fluid)
+        LBM_CUDA_TRY(cudaMemsetAsync(s.fluid_cell + s.n_fluid, 0, sizeof(int32_t) * (s.n_pad - s.n_fluid), st));
+    k_neighbours<<<fblk, kBlock, 0, st>>>(d_idx, s.fluid_cell, s.n_fluid, s.n_pad, nx, ny, nz,
+                                          s.box.periodic_z, s.nbr, s.lmask, d_wcnt);
+    LBM_CUDA_TRY(cudaMemcpyAsync(s.warp_off, d_wcnt, sizeof(uint32_t) * (s.n_pad / 32), cudaMemcpyDeviceToDevice, st));
+    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(s.warp_off, s.n_pad / 32, d_total + 1);
+    LBM_CUDA_TRY(cudaGetLastError());
+
+    LinkArgs la{s.fluid_cell, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, s.n_fluid,
+                nx, ny, nz, s.box.periodic_z, bins.nbx, bins.nby, s.box.q_lo, s.box.q_hi};
+    k_links<<<fblk, kBlock, 0, st>>>(la);
+    LBM_CUDA_TRY(cudaMemsetAsync(s.plane_off, 0, sizeof(int32_t) * (nz + 1), st));
+    if (s.n_fluid > 0)
+        k_plane_offsets<<<(unsigned)((s.n_fluid + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+            s.fluid_cell, s.n_fluid, nx * ny, nz, s.plane_off);
+    LBM_CUDA_TRY(cudaGetLastError());
+
+    uint32_t totals[2] = {0, 0};
+    LBM_CUDA_TRY(cudaMemcpyAsync(totals, d_total, sizeof(totals), cudaMemcpyDeviceToHost, st));
+    LBM_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((int64_t)totals[0] != s.n_fluid || (int64_t)totals[1] != s.n_links) {
+        std::fprintf(stderr, "liblbm: device list build disagrees with host counts (%u/%lld fluid, %u/%lld links)\n",
+                     totals[0], (long long)s.n_fluid, totals[1], (long long)s.n_links);
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
+}
+
+}  // namespace lbm

@@ -1,0 +1,91 @@
+"""CPU-side checks of the C-ABI library: it builds, loads and exports every
+symbol of include/lbm.h, and its host geometry (sphere placement, voxel mask)
+equals the oracle's bit for bit.  No GPU kernel is launched here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1507_06565_gb300 as L
+from paper_1507_06565_gb300 import workloads as W
+from paper_1507_06565_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return L.load_library()
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(lib):
+    declared = _declared_symbols()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(L.SIGNATURES) == declared
+
+
+def test_status_strings(lib):
+    for code in range(-8, 1):
+        assert L.status_string(code) != "unknown status"
+
+
+@pytest.mark.parametrize("case", W.small_cases() + [W.W4_cube(0), W.W4_cube(1)], ids=lambda c: c.name)
+def test_sphere_placement_and_mask_bit_exact(lib, case):
+    sp_o, phi_o, rc = O.place_spheres(*case.sphere_args())
+    assert rc == 0
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args(), q_lo=case.q_lo, q_hi=case.q_hi)
+    sp = geom.spheres()
+    assert sp.shape == sp_o.shape and np.array_equal(sp, sp_o)
+    assert geom.info()["porosity"] == phi_o
+    mask_o = O.voxelize(case.nx, case.ny, case.nz, case.periodic_z, sp_o)
+    assert np.array_equal(geom.mask(), mask_o)
+    lists = O.build_lists(case.nx, case.ny, case.nz, case.periodic_z, sp_o, case.q_lo, case.q_hi, use_bins=True)
+    inf = geom.info()
+    assert inf["n_fluid"] == len(lists["fluid_cell"]) and inf["n_links"] == len(lists["link_k"])
+
+
+@pytest.mark.parametrize("phi", W.W2_POROSITIES)
+def test_full_size_channel_spheres_bit_exact(lib, phi):
+    """The 256x256x512 channel packings: same sphere list and voxel count."""
+    case = W.W2(phi)
+    sp_o, phi_o, rc = O.place_spheres(*case.sphere_args())
+    assert rc == 0
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+    assert np.array_equal(geom.spheres(), sp_o)
+    assert geom.info()["porosity"] == phi_o
+    assert phi_o <= phi
+
+
+def test_explicit_list_geometry(lib):
+    sp = np.array([[5.25, 4.5, 3.0, 2.5], [-0.5, 0.25, 6.0, 1.75]])
+    geom = L.lbm_geometry_from_list(10, 9, 12, False, sp)
+    assert np.array_equal(geom.mask(), O.voxelize(10, 9, 12, False, sp))
+    assert np.array_equal(geom.spheres(), sp)
+
+
+def test_error_codes(lib):
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_geometry_from_spheres(24, 24, 24, True, 0.0, 24.0, 4.0, 4.0, 0.1, False, 3, max_rejects=2000)
+    assert e.value.status == L.LBM_EPACKING
+    with pytest.raises(L.LBMError) as e:   # 2r >= nx
+        L.lbm_geometry_from_spheres(8, 8, 8, True, 0.0, 8.0, 4.0, 4.0, 0.5, True, 3)
+    assert e.value.status == L.LBM_EINVAL
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_geometry_from_list(8, 8, 8, False, [[1.0, 1.0, 1.0, -1.0]])
+    assert e.value.status == L.LBM_EINVAL
+    geom = L.lbm_geometry_from_list(8, 8, 8, False, [])
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_workspace_size(geom, L.make_params(tau=0.5))
+    assert e.value.status == L.LBM_EINVAL
+    assert L.lbm_workspace_size(geom, L.make_params()) > 0

@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer and index results (fluid list, neighbour table, link list, link
+fractions q) must be bit-exact.  Floating-point fields in FP32 storage must
+agree to 1e-5 of the largest velocity (or population) of the oracle, the
+tolerance of the FP32 path; permeability to 1e-4 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1507_06565_gb300 as L
+from paper_1507_06565_gb300 import workloads as W
+from paper_1507_06565_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+TOL_U = 1e-5      # |u - u_oracle|_inf <= TOL_U * max|u_oracle|
+TOL_K = 1e-4      # relative permeability
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build()
+    L.load_library()
+    return torch
+
+
+def _pair(torch, case, storage="f32", u0=None, g=None):
+    g = case.g if g is None else g
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args(), q_lo=case.q_lo, q_hi=case.q_hi)
+    sp = geom.spheres()
+    u0_t = None if u0 is None else torch.from_numpy(u0).cuda()
+    solver = L.Solver(geom, case.tau, case.lam, g, storage, u0=u0_t)
+    lat = O.Lattice(case.nx, case.ny, case.nz, case.periodic_z, sp, case.tau, case.lam, g, case.q_lo,
+                    case.q_hi).init(None if u0 is None else u0.astype(np.float64))
+    return solver, lat, geom
+
+
+def _oracle_shifted(lat, fluid_cell):
+    _, w = O.velocity_set()
+    f = lat.get_f().reshape(19, -1)[:, fluid_cell]
+    return f - w[:, None]
+
+
+CASES = W.small_cases()
+
+
+@pytest.mark.parametrize("case", CASES + [W.W4_cube(0)], ids=lambda c: c.name)
+def test_lists_bit_exact(torch_cuda, case):
+    solver, _, geom = _pair(torch_cuda, case)
+    got = solver.export_lists()
+    want = O.build_lists(case.nx, case.ny, case.nz, case.periodic_z, geom.spheres(), case.q_lo, case.q_hi,
+                         use_bins=True)
+    for key in want:
+        assert got[key].dtype == want[key].dtype, key
+        assert np.array_equal(got[key], want[key]), key
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 3, 10])
+def test_populations_step_by_step(torch_cuda, case, nsteps):
+    """Both AA parities: the shifted populations after n steps from a warm
+    start, at every fluid cell and direction."""
+    u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=100 + nsteps, amplitude=2e-2)
+    solver, lat, _ = _pair(torch_cuda, case, u0=u0, g=(3e-5, -1e-5, 2e-5))
+    solver.step(nsteps)
+    lat.step(nsteps)
+    fluid = solver.export_lists()["fluid_cell"]
+    got = solver.populations().cpu().numpy().astype(np.float64)
+    want = _oracle_shifted(lat, fluid)
+    assert np.max(np.abs(got - want)) <= TOL_U * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+@pytest.mark.parametrize("nsteps", [40, 41])
+def test_moments_and_plane_average(torch_cuda, case, nsteps):
+    """Dense moments and plane averages at both parities after a warm start.
+    The force is large enough that its per-step increment is resolved by FP32
+    storage next to the warm-start populations (see the FP32 regime note)."""
+    u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=7, amplitude=1e-2)
+    solver, lat, geom = _pair(torch_cuda, case, u0=u0, g=(3e-5, -1e-5, 2e-5))
+    solver.step(nsteps)
+    lat.step(nsteps)
+    rho, u = solver.moments()
+    rho_o, u_o = lat.moments()
+    solid = geom.mask().astype(bool)
+    assert np.all(rho.cpu().numpy()[solid] == 0) and np.all(u.cpu().numpy()[:, solid] == 0)
+    umax = np.max(np.abs(u_o))
+    assert np.max(np.abs(u.cpu().numpy() - u_o)) <= TOL_U * umax
+    assert np.max(np.abs(rho.cpu().numpy() - rho_o)[~solid]) <= 1e-6
+    pa, pa_o = solver.plane_average(), lat.plane_average()
+    assert np.array_equal(pa[:, 2], pa_o[:, 2])
+    assert np.max(np.abs(pa[:, :2] - pa_o[:, :2])) <= TOL_U * umax
+
+
+def test_w1_2000_steps_velocity(torch_cuda):
+    """32x32x64 channel with RSA spheres, cold start, 2000 steps (FP32)."""
+    case = W.W1
+    solver, lat, _ = _pair(torch_cuda, case)
+    solver.step(case.steps)
+    lat.step(case.steps)
+    _, u = solver.moments()
+    _, u_o = lat.moments()
+    umax = np.max(np.abs(u_o[0]))
+    assert umax > 0
+    assert np.max(np.abs(u.cpu().numpy() - u_o)) <= TOL_U * umax
+    pa, pa_o = solver.plane_average(), lat.plane_average()
+    assert np.max(np.abs(pa[:, 0] - pa_o[:, 0])) <= TOL_U * np.max(np.abs(pa_o[:, 0]))
+
+
+@pytest.mark.parametrize("tau,lam,q_lo,q_hi", [(0.8, 3 / 16, 0.5, 0.5), (1.4, 3 / 16, 0.3, 0.8),
+                                               (0.8, 0.25, 0.15, 1.0)])
+def test_channel_closed_form_on_gpu(torch_cuda, tau, lam, q_lo, q_hi):
+    """Steady channel against the closed form of the CLI wall slip,
+    u(z_w) = -(g/nu)(q^2/2 - 2 Lambda/3), in FP32 storage."""
+    nz, g = 18, 1e-6
+    geom = L.lbm_geometry_from_list(4, 4, nz, False, [], q_lo=q_lo, q_hi=q_hi)
+    solver = L.Solver(geom, tau, lam, (g, 0.0, 0.0))
+    nu = (tau - 0.5) / 3
+    H = nz - 2
+    solver.step(int(40 * H * H / (math.pi ** 2 * nu)) + 201)
+    _, u = solver.moments()
+    ux = u[0, 1:nz - 1, 0, 0].cpu().numpy().astype(np.float64)
+    z = np.arange(1, nz - 1, dtype=np.float64)
+    za, zb = 1 - q_lo, nz - 2 + q_hi
+    ua = -(g / nu) * (q_lo ** 2 / 2 - 2 * lam / 3)
+    ub = -(g / nu) * (q_hi ** 2 / 2 - 2 * lam / 3)
+    exact = g / (2 * nu) * (z - za) * (zb - z) + ua + (ub - ua) * (z - za) / (zb - za)
+    assert np.max(np.abs(ux - exact)) <= TOL_U * np.max(exact)
+
+
+def test_permeability_converged(torch_cuda):
+    """Periodic sphere cube run to a plane-profile residual of 1e-9 on the GPU;
+    the oracle takes the same number of steps (step-exact parity) and the
+    permeabilities must agree to 1e-4.  g = 1e-4 keeps the pore velocities
+    (~1e-3) in the range FP32 storage resolves; K does not depend on g in the
+    Stokes regime."""
+    case = CASES[2]
+    g = (1e-4, 0.0, 0.0)
+    solver, lat, _ = _pair(torch_cuda, case, g=g)
+    rc, n, res = solver.run_until(1e-9, 100, 200000, criterion="profile")
+    assert rc == L.LBM_OK, (rc, n, res)
+    lat.step(n)
+    k, k_o = solver.permeability(), lat.permeability()
+    assert abs(k / k_o - 1) <= TOL_K
+    # converged: the oracle's profile moves by less than 1e-8 over 100 more steps
+    p0 = lat.plane_average()[:, 0]
+    lat.step(100)
+    p1 = lat.plane_average()[:, 0]
+    assert np.linalg.norm(p1 - p0) / np.linalg.norm(p1) < 1e-8
+
+
+def test_recenter_keeps_velocity(torch_cuda):
+    """A uniform density shift commutes with the whole update: after
+    re-centring, the velocities stay on the oracle's (which never re-centres)
+    and the mean density deviation drops to round-off."""
+    case = CASES[2]
+    g = (1e-4, 0.0, 0.0)
+    solver, lat, _ = _pair(torch_cuda, case, g=g)
+    solver.step(3000)
+    lat.step(3000)
+    drift = solver.mass()
+    rho_o, _ = lat.moments()
+    fl = lat.solid() == 0
+    assert abs(drift - (rho_o[fl].mean() - 1.0)) <= 1e-5 * abs(drift)   # CLI mass drift, reported
+    assert abs(drift) > 1e-6
+    solver.recenter()
+    solver.step(101)
+    lat.step(101)
+    assert abs(solver.mass()) < 1e-6 * abs(drift) + 1e-9
+    _, u = solver.moments()
+    _, u_o = lat.moments()
+    assert np.max(np.abs(u.cpu().numpy() - u_o)) <= TOL_U * np.max(np.abs(u_o))
+
+
+def test_profile_residual_matches_oracle(torch_cuda):
+    case = W.W1
+    solver, lat, _ = _pair(torch_cuda, case)
+    assert math.isinf(solver.profile_residual())
+    p0 = lat.plane_average()[:, 0]
+    solver.step(300)
+    lat.step(300)
+    p1 = lat.plane_average()[:, 0]
+    want = np.linalg.norm(p1 - p0) / np.linalg.norm(p1)
+    assert abs(solver.profile_residual() / want - 1) < 1e-4
+
+
+def test_permeability_window(torch_cuda):
+    case = W.W1
+    solver, lat, _ = _pair(torch_cuda, case)
+    solver.step(500)
+    lat.step(500)
+    for zl, zh in [(-1, -1), (3, 20), (40, 40)]:
+        assert abs(solver.permeability(zl, zh) / lat.permeability(zl, zh) - 1) <= TOL_K
+    with pytest.raises(L.LBMError):
+        solver.permeability(10, 64)
+
+
+def test_residual_semantics(torch_cuda):
+    case = CASES[1]
+    solver, lat, _ = _pair(torch_cuda, case)
+    assert math.isinf(solver.residual())
+    lat.residual()
+    solver.step(50)
+    lat.step(50)
+    r, r_o = solver.residual(), lat.residual()
+    assert abs(r / r_o - 1) < 1e-3
+
+
+def test_nan_is_reported(torch_cuda):
+    """A non-finite warm start (host-made input) surfaces as LBM_ENAN."""
+    case = CASES[1]
+    u0 = np.zeros((3, case.nz, case.ny, case.nx), np.float32)
+    u0[0, 10] = np.nan   # a plane of the free channel above the packing
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+    import torch
+
+    solver = L.Solver(geom, u0=torch.from_numpy(u0).cuda())
+    solver.step(3)
+    with pytest.raises(L.LBMError) as e:
+        solver.residual()
+    assert e.value.status == L.LBM_ENAN
+
+
+def test_workspace_too_small(torch_cuda):
+    torch = torch_cuda
+    geom = L.lbm_geometry_from_spheres(*CASES[1].sphere_args())
+    p = L.make_params()
+    n = L.lbm_workspace_size(geom, p)
+    ws = torch.empty(n - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_init(geom, p, ws)
+    assert e.value.status == L.LBM_ESIZE
+
+
+def test_step_zero_and_reset(torch_cuda):
+    case = CASES[1]
+    solver, lat, _ = _pair(torch_cuda, case)
+    solver.step(0)
+    h0 = solver.populations().cpu().numpy()
+    solver.step(7)
+    solver.reset()
+    assert solver.steps == 0
+    assert np.array_equal(solver.populations().cpu().numpy(), h0)
