@@ -29,10 +29,9 @@ sys.path.insert(0, ROOT)
 
 from paper_1507_06565_gb300 import workloads as W  # noqa: E402
 
-STORED_BYTES_F32 = 19 * 2 * 4   # algorithmic bytes per fluid lattice update (19 reads + 19 writes)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-METRIC = "fluid MLUPS (D3Q19 TRT + CLI stream-collide, % of HBM roofline in 'roofline')"
+METRIC = "fluid MLUPS (D3Q19 TRT + CLI stream-collide; HBM roofline fraction in 'roofline')"
 WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlapping r=8 spheres, "
             "porosity sweep {0.4,0.6,0.8,0.9} (one solver each); one step = one time step of all four")
 # bounded samples of the workload for the CPU oracle: same sphere radius,
@@ -184,7 +183,7 @@ def run_ours(args, world, rank, local):
         cases = [W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True,
                            W.W2(phi).seed) for phi in W.W2_POROSITIES]
     geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
-    solvers = [L.Solver(g, c.tau, c.lam, c.g, "f32") for g, c in zip(geoms, cases)]
+    solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage) for g, c in zip(geoms, cases)]
     nfs = [s.info()["n_fluid"] for s in solvers]
     nf_total = sum(nfs)
     lib = L.load_library()
@@ -226,8 +225,9 @@ def run_ours(args, world, rank, local):
         ms = float(tt.item())
     durs = np.array([a.elapsed_time(b) for a, b in zip(*ev)]).reshape(args.steps, len(solvers))
     first_parity = args.warmup & 1   # parity of the first timed step
-    # per-launch algorithmic bytes: 152 B per fluid cell (19 loads + 19 stores of FP32)
-    bytes_per_launch = np.array(nfs, dtype=np.float64) * STORED_BYTES_F32
+    # per-launch algorithmic bytes: 19 loads + 19 stores of the stored type per fluid cell
+    bytes_per_flup = 19 * 2 * (4 if args.storage == "f32" else 2)
+    bytes_per_launch = np.array(nfs, dtype=np.float64) * bytes_per_flup
     achieved = float((bytes_per_launch[None, :] / (durs * 1e-3)).mean() / 1e9)
     parity = {}
     for off in (0, 1):
@@ -247,7 +247,7 @@ def run_ours(args, world, rank, local):
     h2d = 0
     d2h = 0
     for g, c in zip(geoms, cases):
-        s2 = L.Solver(g, c.tau, c.lam, c.g, "f32")
+        s2 = L.Solver(g, c.tau, c.lam, c.g, args.storage)
         s2.step(e2e_steps)
         pa = s2.plane_average()
         h2d += g.mask().nbytes
@@ -260,15 +260,15 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == "channel" else WORKLOAD.replace("256x256x512", "128x128x256"),
-                   "fluid_cells": nfs, "storage": "f32",
+                   "fluid_cells": nfs, "storage": args.storage,
                    "l2": "inputs larger than L2 (4.1-5.7 GB of populations and indices per solver)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_step_even/k_step_odd (fused AA stream-collide + CLI)",
-                     "bytes_per_flup": STORED_BYTES_F32, "peak_kind": peak_kind, "by_parity": parity},
+                     "bytes_per_flup": bytes_per_flup, "peak_kind": peak_kind, "by_parity": parity},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "what": f"lbm_init from host geometry + {e2e_steps} steps + plane averages to host, all four solvers"},
@@ -291,6 +291,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+                    help="population storage (FP32 collision in every case)")
     ap.add_argument("--workload", choices=["channel", "channel-half"], default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for profiling")
     args = ap.parse_args()

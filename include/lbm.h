@@ -92,17 +92,28 @@ typedef struct {
     int64_t max_rejects;
 } lbm_sphere_params;
 
+/* Variant of the odd (gather/scatter) step; both address the same slots and
+ * differ only in FP32 rounding.  LBM_FLAG_NEIGHBOUR_TABLE reads the 18 neighbour indices of a cell
+ * from the stored table (72 bytes per cell and odd step);
+ * LBM_FLAG_ROW_NEIGHBOURS computes them from per-row fluid bitmasks (about
+ * 4 bytes per cell).  Neither: the library picks the table for FP32 storage
+ * and the bitmasks for 16-bit storage.  The table is used whenever ny*nz does
+ * not fit beside x in 32 bits. */
+#define LBM_FLAG_NEIGHBOUR_TABLE 1
+#define LBM_FLAG_ROW_NEIGHBOURS 2
+
 /* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
  * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes
  * omega- (Sec. 2.1; 3/16 puts bounce-back walls exactly half-way).  g is the
  * body force per unit mass (the source F_k = 3 w_k e_k.g of Eq. (collision)).
- * storage is LBM_F32, LBM_F16 or LBM_BF16. */
+ * storage is LBM_F32, LBM_F16 or LBM_BF16; flags is 0 or one of the
+ * LBM_FLAG_* variants above. */
 typedef struct {
     double tau;
     double lambda;
     double g[3];
     int32_t storage;
-    int32_t reserved;
+    int32_t flags;
 } lbm_params;
 
 typedef struct {

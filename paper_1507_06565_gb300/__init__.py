@@ -30,6 +30,9 @@ LBM_ENOTCONVERGED = -6
 LBM_ETIMEOUT = -7
 LBM_ESIZE = -8
 
+LBM_FLAG_NEIGHBOUR_TABLE = 1
+LBM_FLAG_ROW_NEIGHBOURS = 2
+
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1
 
@@ -59,7 +62,7 @@ class lbm_sphere_params(ctypes.Structure):
 
 class lbm_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("lambda_", ctypes.c_double), ("g", ctypes.c_double * 3),
-                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class lbm_geometry_info(ctypes.Structure):
@@ -212,9 +215,9 @@ def lbm_geometry_from_list(nx, ny, nz, periodic_z, xyzr, q_lo=0.5, q_hi=0.5) -> 
 # ---------------------------------------------------------------------------
 # Solver
 # ---------------------------------------------------------------------------
-def make_params(tau=0.8, lam=3.0 / 16.0, g=(1e-6, 0.0, 0.0), storage="f32") -> lbm_params:
+def make_params(tau=0.8, lam=3.0 / 16.0, g=(1e-6, 0.0, 0.0), storage="f32", flags=0) -> lbm_params:
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
-    return lbm_params(float(tau), float(lam), (ctypes.c_double * 3)(*[float(v) for v in g]), st, 0)
+    return lbm_params(float(tau), float(lam), (ctypes.c_double * 3)(*[float(v) for v in g]), st, int(flags))
 
 
 def lbm_workspace_size(geom: Geometry, params: lbm_params) -> int:
@@ -237,10 +240,10 @@ class Solver:
     """A solver handle with its caller-owned workspace (a torch uint8 tensor)."""
 
     def __init__(self, geom: Geometry, tau=0.8, lam=3.0 / 16.0, g=(1e-6, 0.0, 0.0), storage="f32", u0=None,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, flags=0):
         import torch
 
-        self.params = make_params(tau, lam, g, storage)
+        self.params = make_params(tau, lam, g, storage, flags)
         self.box = geom.box
         self.shape = geom.shape
         nbytes = lbm_workspace_size(geom, self.params)

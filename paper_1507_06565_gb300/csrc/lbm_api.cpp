@@ -40,6 +40,8 @@ Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int sto
     L.link_q = take((size_t)(n_links > 0 ? n_links : 1) * 8);
     L.fluid_cell = take((size_t)n_pad * 4);
     L.plane_off = take((size_t)(box.nz + 1) * 4);
+    L.row_words = take((size_t)box.ny * box.nz * ((box.nx + 31) / 32) * 8);
+    L.cell_xr = take((size_t)n_pad * 4);
     L.u_cur = take((size_t)3 * n_pad * 4);
     L.u_prev = take((size_t)3 * n_pad * 4);
     L.rho_cur = take((size_t)n_pad * 4);
@@ -53,6 +55,27 @@ Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int sto
     return L;
 }
 
+int x_bits_for(int nx)
+{
+    int b = 1;
+    while ((1 << b) < nx) ++b;
+    return b;
+}
+
+bool rows_packable(const lbm_box &box)
+{
+    const int xb = x_bits_for(box.nx);
+    return (int64_t)box.ny * box.nz <= ((int64_t)1 << (32 - xb));
+}
+
+// The kernels address populations with 32-bit element offsets (19 n_pad <
+// 2^32, about 226 million fluid cells) and links with 32-bit indices.
+static bool size_ok(const Geometry &g)
+{
+    const int64_t n_pad = (g.n_fluid + kBlock - 1) / kBlock * kBlock;
+    return (int64_t)kQ * n_pad < ((int64_t)1 << 32) && g.n_links <= (int64_t)std::numeric_limits<uint32_t>::max();
+}
+
 static bool params_ok(const lbm_params *p)
 {
     if (!p) return false;
@@ -60,6 +83,7 @@ static bool params_ok(const lbm_params *p)
     if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return false;
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return false;
+    if (p->flags != 0 && p->flags != LBM_FLAG_NEIGHBOUR_TABLE && p->flags != LBM_FLAG_ROW_NEIGHBOURS) return false;
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
 }
 
@@ -155,8 +179,7 @@ void lbm_geometry_destroy(lbm_geometry *g) { delete g; }
 int lbm_workspace_size(const lbm_geometry *g, const lbm_params *params, size_t *bytes)
 {
     if (!g || !bytes || !params_ok(params)) return LBM_EINVAL;
-    if (g->n_fluid > (int64_t)std::numeric_limits<int32_t>::max() - kBlock) return LBM_EINVAL;
-    if (g->n_links > (int64_t)std::numeric_limits<uint32_t>::max()) return LBM_EINVAL;
+    if (!size_ok(*g)) return LBM_EINVAL;
     Bins bins;
     const int rc = bins_for(*g, bins);
     if (rc != LBM_OK) return rc;
@@ -170,8 +193,7 @@ int lbm_init(const lbm_geometry *g, const lbm_params *params, void *dev_workspac
 {
     if (!g || !out || !params_ok(params)) return LBM_EINVAL;
     *out = nullptr;
-    if (g->n_fluid > (int64_t)std::numeric_limits<int32_t>::max() - kBlock) return LBM_EINVAL;
-    if (g->n_links > (int64_t)std::numeric_limits<uint32_t>::max()) return LBM_EINVAL;
+    if (!size_ok(*g)) return LBM_EINVAL;
     if (!dev_workspace || ((uintptr_t)dev_workspace & 255u) != 0) return LBM_ESIZE;
     Bins bins;
     int rc = bins_for(*g, bins);
@@ -202,6 +224,16 @@ int lbm_init(const lbm_geometry *g, const lbm_params *params, void *dev_workspac
     s->link_q = (double *)(s->ws + L.link_q);
     s->fluid_cell = (int32_t *)(s->ws + L.fluid_cell);
     s->plane_off = (int32_t *)(s->ws + L.plane_off);
+    s->row_words = (uint2 *)(s->ws + L.row_words);
+    s->cell_xr = (uint32_t *)(s->ws + L.cell_xr);
+    s->n_words = (g->box.nx + 31) / 32;
+    s->x_bits = x_bits_for(g->box.nx);
+    {
+        bool rows = params->storage != LBM_F32;   // auto: see LBM_FLAG_* in lbm.h
+        if (params->flags == LBM_FLAG_NEIGHBOUR_TABLE) rows = false;
+        if (params->flags == LBM_FLAG_ROW_NEIGHBOURS) rows = true;
+        s->odd_rows = rows && rows_packable(g->box);
+    }
     s->u_cur = (float *)(s->ws + L.u_cur);
     s->u_prev = (float *)(s->ws + L.u_prev);
     s->rho_cur = (float *)(s->ws + L.rho_cur);

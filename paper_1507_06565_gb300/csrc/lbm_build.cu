@@ -92,17 +92,42 @@ __global__ void k_fill_index(const uint8_t *__restrict__ mask, int64_t ncell,
     }
 }
 
-// 3. neighbour table, link mask, link count per aligned group of 32 cells
+// Row bitmask words: one thread per (row, word) of 32 cells along x.
+__global__ void k_row_words(const int32_t *__restrict__ idx_map, int nx, int64_t nrows, int nw,
+                            uint2 *__restrict__ words)
+{
+    const int64_t t = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (t >= nrows * nw) return;
+    const int64_t row = t / nw;
+    const int w = (int)(t % nw);
+    uint32_t bits = 0, base = 0;
+    bool seen = false;
+    for (int b = 0; b < 32; ++b) {
+        const int x = 32 * w + b;
+        if (x >= nx) break;
+        const int32_t j = idx_map[row * nx + x];
+        if (j >= 0) {
+            bits |= 1u << b;
+            if (!seen) base = (uint32_t)j;
+            seen = true;
+        }
+    }
+    words[t] = make_uint2(bits, base);
+}
+
+// 3. neighbour table, link mask, link count per aligned group of 32 cells,
+//    packed (x, row) of each fluid cell
 __global__ void k_neighbours(const int32_t *__restrict__ idx_map, const int32_t *__restrict__ fluid_cell,
                              int32_t n_fluid, int32_t n_pad, int nx, int ny, int nz, int periodic_z,
-                             int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
-                             uint32_t *__restrict__ warp_cnt)
+                             int x_bits, int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
+                             uint32_t *__restrict__ warp_cnt, uint32_t *__restrict__ cell_xr)
 {
     const int32_t i = blockIdx.x * kBlock + threadIdx.x;
     uint32_t m = 0;
     if (i < n_fluid) {
         const int32_t c = fluid_cell[i];
         const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+        cell_xr[i] = (uint32_t)x | ((uint32_t)(c / nx) << x_bits);
 #pragma unroll
         for (int k = 1; k < kQ; ++k) {
             const int xn = wrap(x + ex(k), nx), yn = wrap(y + ey(k), ny);
@@ -115,6 +140,7 @@ __global__ void k_neighbours(const int32_t *__restrict__ idx_map, const int32_t 
         }
     } else if (i < n_pad) {
         for (int k = 1; k < kQ; ++k) nbr[(size_t)(k - 1) * n_pad + i] = -1;
+        cell_xr[i] = 0;
     }
     if (i < n_pad) lmask[i] = m;
     uint32_t cnt = __popc(m);
@@ -250,7 +276,12 @@ int device_build(Solver &s, const Geometry &g, const Bins &bins)
     if (s.n_pad > s.n_fluid)
         LBM_CUDA_TRY(cudaMemsetAsync(s.fluid_cell + s.n_fluid, 0, sizeof(int32_t) * (s.n_pad - s.n_fluid), st));
     k_neighbours<<<fblk, kBlock, 0, st>>>(d_idx, s.fluid_cell, s.n_fluid, s.n_pad, nx, ny, nz,
-                                          s.box.periodic_z, s.nbr, s.lmask, d_wcnt);
+                                          s.box.periodic_z, s.x_bits, s.nbr, s.lmask, d_wcnt, s.cell_xr);
+    {
+        const int64_t nrows = (int64_t)ny * nz, nwords = nrows * s.n_words;
+        k_row_words<<<(unsigned)((nwords + kBlock - 1) / kBlock), kBlock, 0, st>>>(d_idx, nx, nrows, s.n_words,
+                                                                                  s.row_words);
+    }
     LBM_CUDA_TRY(cudaMemcpyAsync(s.warp_off, d_wcnt, sizeof(uint32_t) * (s.n_pad / 32), cudaMemcpyDeviceToDevice, st));
     k_scan_exclusive<<<1, kScanThreads, 0, st>>>(s.warp_off, s.n_pad / 32, d_total + 1);
     LBM_CUDA_TRY(cudaGetLastError());

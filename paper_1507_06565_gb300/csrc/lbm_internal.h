@@ -11,6 +11,10 @@
 //   link_q     [n_links]    double, link fraction q (kept for export)
 //   fluid_cell [n_pad]      int32 cell index c = x + nx (y + ny z)
 //   plane_off  [nz+1]       int32 first fluid index of each z plane
+//   row_words  [ny*nz][nw]  uint2 per 32-cell word of each x-row (y, z):
+//                           {fluid bitmask, fluid index of its first fluid cell};
+//                           a neighbour's index is base + popc(bits below x)
+//   cell_xr    [n_pad]      uint32 x | (row << x_bits), row = y + ny z
 //   u_cur/u_prev [3][n_pad] float velocity snapshots (fluid order), rho_cur [n_pad]
 //                           holds rho - 1
 // Links of a cell are stored in increasing k; cells in fluid order, so the
@@ -80,7 +84,7 @@ struct Bins {
 
 // Workspace carve-up.
 struct Layout {
-    size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off;
+    size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr;
     size_t u_cur, u_prev, rho_cur, prof_prev, bins_start, bins_img, scan_tmp, partials, result, total;
     // build-time aliases inside the pdf region
     size_t idx_map, mask;
@@ -105,6 +109,9 @@ struct Solver {
     double omega_p = 0, omega_m = 0, nu = 0;
     double drho_shift = 0;   // uniform density shift applied by the next step
     int nbins_x = 0, nbins_y = 0, nbins_z = 0;
+    int n_words = 0;          // 32-cell words per row
+    int x_bits = 0;           // bits of x in cell_xr
+    bool odd_rows = true;     // odd step computes neighbours from row bitmasks
     // device pointers
     void *pdf = nullptr;
     int32_t *nbr = nullptr;
@@ -114,6 +121,8 @@ struct Solver {
     double *link_q = nullptr;
     int32_t *fluid_cell = nullptr;
     int32_t *plane_off = nullptr;
+    uint2 *row_words = nullptr;
+    uint32_t *cell_xr = nullptr;
     float *u_cur = nullptr;
     float *u_prev = nullptr;
     float *rho_cur = nullptr;
@@ -131,6 +140,9 @@ void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bi
 // ---- workspace (lbm_api.cpp) ----
 Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int storage,
                    size_t n_bins, size_t n_images);
+// bits needed for x in cell_xr; rows must fit in the remaining bits
+int x_bits_for(int nx);
+bool rows_packable(const lbm_box &box);
 
 // ---- device build (lbm_build.cu) ----
 int device_build(Solver &s, const Geometry &g, const Bins &bins);

@@ -32,11 +32,17 @@
 namespace lbm {
 
 // ---- storage conversions ----
+// Shifted populations are small (|h| << 1).  FP16 stores them scaled by 2^14
+// (exact) so that values down to ~4e-9 stay normal numbers with the full
+// 11-bit significand; |h| < 4 keeps them below the FP16 maximum.  BF16 shares
+// the FP32 exponent range and is stored unscaled.
+constexpr float kHalfScale = 16384.0f;
+constexpr float kHalfUnscale = 1.0f / 16384.0f;
 __device__ __forceinline__ float ld(const float *p) { return *p; }
-__device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float ld(const __half *p) { return __half2float(*p) * kHalfUnscale; }
 __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 // Relaxation constants and source term of one solver (kernel parameter).
@@ -83,6 +89,31 @@ __device__ __forceinline__ void load_links(float a[kQ], uint32_t m, const float 
         a[k] = 0.0f;
         if ((m >> k) & 1u) a[k] = link_a[off++];
     }
+}
+
+// Shared-memory staged variants (a_s[k-1][t] holds the coefficient of link k
+// of thread t; each thread touches only its own column).
+__device__ __forceinline__ void stage_links(float (*a_s)[kBlock], int t, uint32_t m,
+                                            const float *__restrict__ link_a, uint32_t off)
+{
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) {
+        float v = 0.0f;
+        if ((m >> k) & 1u) v = link_a[off++];
+        a_s[k - 1][t] = v;
+    }
+}
+
+__device__ __forceinline__ void cli_incoming_s(float h[kQ], const float (*a_s)[kBlock], int t)
+{
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(a_s[k - 1][t], h[k], h[opp(k)]);
+}
+
+__device__ __forceinline__ void cli_outgoing_s(float h[kQ], const float (*a_s)[kBlock], int t)
+{
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) h[k] = fmaf(-a_s[k - 1][t], h[opp(k)], h[k]);
 }
 
 // Completes the incoming populations of link-reverse directions:
@@ -165,6 +196,70 @@ __device__ __forceinline__ void gather_odd(float h[kQ], const T *__restrict__ pd
         const T *src = up >= 0 ? pdf + opp(k) * n_pad + up : pdf + k * n_pad + i;
         h[k] = ld(src);
     }
+}
+
+// Geometry of the row bitmasks (see lbm_internal.h).
+struct RowGeo {
+    const uint2 *words;
+    const uint32_t *cell_xr;
+    int nx, ny, nz, nw, x_bits, periodic_z;
+};
+
+// Fluid index of bit b of a row word, -1 when the cell is solid.
+__device__ __forceinline__ int32_t word_pick(uint2 w, int b)
+{
+    const uint32_t bit = 1u << b;
+    return (w.x & bit) ? (int32_t)(w.y + __popc(w.x & (bit - 1u))) : -1;
+}
+
+// Fluid indices of x-1, x, x+1 (periodic in x) in the row whose words start at
+// `row`: one word load, plus the neighbouring word at a word edge.
+__device__ __forceinline__ void row_triple(const RowGeo &g, const uint2 *row, int x, int xm, int xp, int32_t &im,
+                                           int32_t &i0, int32_t &ip)
+{
+    const int b = x & 31;
+    const uint2 c = __ldg(row + (x >> 5));
+    i0 = word_pick(c, b);
+    im = b > 0 ? word_pick(c, b - 1) : word_pick(__ldg(row + (xm >> 5)), xm & 31);
+    ip = (b < 31 && x + 1 < g.nx) ? word_pick(c, b + 1) : word_pick(__ldg(row + (xp >> 5)), xp & 31);
+}
+
+// Neighbour indices of a fluid cell from the row bitmasks: the neighbour
+// (x', y', z') is fluid when bit x' of row (y', z') is set, and its fluid index
+// is the word's base plus the fluid cells below x' in the word.  Writes nb[k]
+// (-1: solid) and returns the link mask (bit k: x + e_k solid).  Fluid cells
+// never lie in a wall layer, so z +- 1 stays in the box when z is not periodic.
+__device__ __forceinline__ uint32_t row_neighbours(int32_t nb[kQ], const RowGeo &g, int32_t i)
+{
+    const uint32_t xr = g.cell_xr[i];
+    const int x = (int)(xr & ((1u << g.x_bits) - 1u));
+    const int row = (int)(xr >> g.x_bits);
+    const int y = row % g.ny, z = row / g.ny;
+    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+    int zm = z - 1, zp = z + 1;
+    if (g.periodic_z) {
+        zm = zm < 0 ? zm + g.nz : zm;
+        zp = zp >= g.nz ? zp - g.nz : zp;
+    }
+    const uint32_t nw = (uint32_t)g.nw, ny = (uint32_t)g.ny;
+    auto R = [&](int yy, int zz) { return g.words + ((uint32_t)yy + ny * (uint32_t)zz) * nw; };
+    int32_t self;
+    nb[0] = i;
+    row_triple(g, R(y, z), x, xm, xp, nb[2], self, nb[1]);       // -x, +x
+    row_triple(g, R(yp, z), x, xm, xp, nb[10], nb[3], nb[7]);    // (-1,1,0) (0,1,0) (1,1,0)
+    row_triple(g, R(ym, z), x, xm, xp, nb[8], nb[4], nb[9]);     // (-1,-1,0) (0,-1,0) (1,-1,0)
+    row_triple(g, R(y, zp), x, xm, xp, nb[14], nb[5], nb[11]);   // (-1,0,1) (0,0,1) (1,0,1)
+    row_triple(g, R(y, zm), x, xm, xp, nb[12], nb[6], nb[13]);   // (-1,0,-1) (0,0,-1) (1,0,-1)
+    const int b = x & 31, w = x >> 5;
+    nb[15] = word_pick(__ldg(R(yp, zp) + w), b);                 // (0,1,1)
+    nb[16] = word_pick(__ldg(R(ym, zm) + w), b);                 // (0,-1,-1)
+    nb[17] = word_pick(__ldg(R(yp, zm) + w), b);                 // (0,1,-1)
+    nb[18] = word_pick(__ldg(R(ym, zp) + w), b);                 // (0,-1,1)
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) m |= (uint32_t)(nb[k] < 0) << k;
+    return m;
 }
 
 __device__ __forceinline__ uint32_t load_nbr(int32_t nb[kQ], const int32_t *__restrict__ nbr, size_t n_pad, int32_t i)
