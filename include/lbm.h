@@ -260,6 +260,27 @@ int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int3
  * dev_out[19][n_fluid] (float).  Asynchronous. */
 int lbm_populations(lbm_solver *solver, float *dev_out);
 
+/* Plane averages without any device allocation (the paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory -- an application whose own pool allocator owns all device memory, or
+ * a monitoring loop that must not stall, since cudaMalloc/cudaFree synchronise
+ * the device).  Same result as lbm_plane_average, computed from a dense
+ * velocity x-component dev_ux[nz][ny][nx] (float, e.g. from lbm_moments) and
+ * the dense solid mask dev_solid[nz][ny][nx] (uint8, 1 = solid) that the
+ * caller already holds on the current device; host_out[nz][3] as in
+ * lbm_plane_average.  The per-plane scratch is a fixed array of
+ * LBM_STATIC_MAX_PLANES planes compiled into the library and kept on every GPU
+ * that loads it until the process exits; nz > LBM_STATIC_MAX_PLANES is
+ * rejected with LBM_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams or threads) race; each call overwrites every entry it uses.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * Synchronises `stream` (a cudaStream_t, NULL = default stream). */
+#define LBM_STATIC_MAX_PLANES 4096
+int lbm_plane_average_static(const float *dev_ux, const uint8_t *dev_solid, int32_t nx, int32_t ny, int32_t nz,
+                             double *host_out, void *stream);
+
 void lbm_solver_destroy(lbm_solver *solver);
 
 const char *lbm_status_string(int status);

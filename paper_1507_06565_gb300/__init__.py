@@ -101,6 +101,7 @@ SIGNATURES = {
     "lbm_solver_info": (_I, [_P, ctypes.POINTER(lbm_geometry_info)]),
     "lbm_export_lists": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "lbm_populations": (_I, [_P, _P]),
+    "lbm_plane_average_static": (_I, [_P, _P, _I32, _I32, _I32, _P, _P]),
     "lbm_solver_destroy": (None, [_P]),
     "lbm_status_string": (ctypes.c_char_p, [_I]),
 }
