@@ -101,13 +101,19 @@ typedef struct {
  * not fit beside x in 32 bits. */
 #define LBM_FLAG_NEIGHBOUR_TABLE 1
 #define LBM_FLAG_ROW_NEIGHBOURS 2
+/* Scheduling switches.  By default lbm_step times a few grid sizes for each
+ * step kernel during its first launches on solvers of more than ~4 waves of
+ * blocks (synchronising the stream while it does so) and then replays the
+ * steps in chunks as a CUDA graph.  These flags turn either off. */
+#define LBM_FLAG_NO_GRAPH 4
+#define LBM_FLAG_NO_AUTOTUNE 8
 
 /* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
  * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes
  * omega- (Sec. 2.1; 3/16 puts bounce-back walls exactly half-way).  g is the
  * body force per unit mass (the source F_k = 3 w_k e_k.g of Eq. (collision)).
- * storage is LBM_F32, LBM_F16 or LBM_BF16; flags is 0 or one of the
- * LBM_FLAG_* variants above. */
+ * storage is LBM_F32, LBM_F16 or LBM_BF16; flags is 0 or an OR of the
+ * LBM_FLAG_* values above (at most one neighbour variant). */
 typedef struct {
     double tau;
     double lambda;
@@ -168,6 +174,40 @@ int lbm_workspace_size(const lbm_geometry *geom, const lbm_params *params, size_
  * after this call.  Errors: LBM_EINVAL, LBM_ESIZE, LBM_ECUDA, LBM_ENOMEM. */
 int lbm_init(const lbm_geometry *geom, const lbm_params *params, void *dev_workspace, size_t bytes,
              const float *dev_u0, void *stream, lbm_solver **out);
+
+/* ------------------------------------------------------------------------- */
+/* Batches: several independent boxes (e.g. periodic REV cubes of uneven     */
+/* size, Sec. 3: the REV scale) advanced together, one kernel launch per     */
+/* step for all of them.  A batch solver answers every call above; its      */
+/* fields are the parts' fields concatenated in part order (cells, fluid     */
+/* cells and z planes), lbm_plane_average returns the parts' planes one      */
+/* after the other, lbm_profile_residual returns the largest part residual,  */
+/* lbm_recenter shifts each part by its own mean density, and                */
+/* lbm_permeability is refused (use lbm_batch_permeability).  The row-bitmask */
+/* neighbour variant is not available for batches.                          */
+/* ------------------------------------------------------------------------- */
+int lbm_batch_workspace_size(const lbm_geometry *const *geoms, int32_t n, const lbm_params *params,
+                             size_t *bytes);
+int lbm_batch_init(const lbm_geometry *const *geoms, int32_t n, const lbm_params *params, void *dev_workspace,
+                   size_t bytes, const float *dev_u0, void *stream, lbm_solver **out);
+int lbm_batch_parts(const lbm_solver *solver, int32_t *n_parts);
+/* Counts of part `part` and the offsets of its first fluid cell, cell and z
+ * plane in the concatenated arrays (any output may be NULL). */
+int lbm_batch_part_info(const lbm_solver *solver, int32_t part, lbm_geometry_info *info, int64_t *fluid_offset,
+                        int64_t *cell_offset, int64_t *plane_offset);
+/* Permeability of every part over its whole box (Eq. (Darcy), as
+ * lbm_permeability with z_lo = z_hi = -1): k_out[n_parts].  Synchronises. */
+int lbm_batch_permeability(lbm_solver *solver, double *k_out);
+/* Profile residual of every part: res_out[n_parts] (+inf on a part's first
+ * call).  Synchronises. */
+int lbm_batch_profile_residual(lbm_solver *solver, double *res_out);
+
+/* Launch schedule in use: grid sizes of the even and odd step kernels (the
+ * kernels loop over tiles of 256 fluid cells, so a grid smaller than the tile
+ * count makes them persistent), whether the autotuner has finished, and the
+ * steps per CUDA-graph replay (0: graphs off). */
+int lbm_schedule(const lbm_solver *solver, int32_t *grid_even, int32_t *grid_odd, int32_t *tuned,
+                 int32_t *graph_steps);
 
 /* Re-initialise the populations of an existing solver (step count back to 0)
  * from dev_u0 (or rest when NULL). */

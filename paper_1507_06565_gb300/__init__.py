@@ -32,6 +32,8 @@ LBM_ESIZE = -8
 
 LBM_FLAG_NEIGHBOUR_TABLE = 1
 LBM_FLAG_ROW_NEIGHBOURS = 2
+LBM_FLAG_NO_GRAPH = 4
+LBM_FLAG_NO_AUTOTUNE = 8
 
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1
@@ -102,6 +104,15 @@ SIGNATURES = {
     "lbm_export_lists": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "lbm_populations": (_I, [_P, _P]),
     "lbm_plane_average_static": (_I, [_P, _P, _I32, _I32, _I32, _P, _P]),
+    "lbm_batch_workspace_size": (_I, [_P, _I32, ctypes.POINTER(lbm_params), ctypes.POINTER(_SZ)]),
+    "lbm_batch_init": (_I, [_P, _I32, ctypes.POINTER(lbm_params), _P, _SZ, _P, _P, ctypes.POINTER(_P)]),
+    "lbm_batch_parts": (_I, [_P, ctypes.POINTER(_I32)]),
+    "lbm_batch_part_info": (_I, [_P, _I32, ctypes.POINTER(lbm_geometry_info), ctypes.POINTER(_I64),
+                                 ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "lbm_batch_permeability": (_I, [_P, _P]),
+    "lbm_batch_profile_residual": (_I, [_P, _P]),
+    "lbm_schedule": (_I, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                          ctypes.POINTER(_I32)]),
     "lbm_solver_destroy": (None, [_P]),
     "lbm_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -351,6 +362,91 @@ class Solver:
         out = torch.empty((19, nf), dtype=torch.float32, device=self.workspace.device)
         _check(load_library().lbm_populations(self._h, _dev_ptr(out)), "lbm_populations")
         return out
+
+
+def _schedule(handle) -> dict:
+    ge, go, tu, gs = _I32(), _I32(), _I32(), _I32()
+    _check(load_library().lbm_schedule(handle, ctypes.byref(ge), ctypes.byref(go), ctypes.byref(tu),
+                                       ctypes.byref(gs)), "lbm_schedule")
+    return {"grid_even": ge.value, "grid_odd": go.value, "tuned": bool(tu.value), "graph_steps": gs.value}
+
+
+Solver.schedule = lambda self: _schedule(self._h)
+
+
+class BatchSolver(Solver):
+    """Several independent boxes advanced together (one launch per step)."""
+
+    def __init__(self, geoms, tau=0.8, lam=3.0 / 16.0, g=(1e-6, 0.0, 0.0), storage="f32", u0=None,
+                 device="cuda", stream=None, flags=0):
+        import torch
+
+        self.params = make_params(tau, lam, g, storage, flags)
+        self.geoms = list(geoms)
+        arr = (_P * len(self.geoms))(*[gm.handle for gm in self.geoms])
+        self._arr = arr
+        n = _SZ()
+        _check(load_library().lbm_batch_workspace_size(arr, len(self.geoms), ctypes.byref(self.params),
+                                                       ctypes.byref(n)), "lbm_batch_workspace_size")
+        self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.workspace.device).cuda_stream
+        self.stream = stream
+        h = _P()
+        _check(load_library().lbm_batch_init(arr, len(self.geoms), ctypes.byref(self.params),
+                                             _dev_ptr(self.workspace), self.workspace.numel(), _dev_ptr(u0),
+                                             ctypes.c_void_p(stream), ctypes.byref(h)), "lbm_batch_init")
+        self._h = h
+        self.box = self.geoms[0].box
+        self.nu = (tau - 0.5) / 3.0
+        self.g = tuple(float(v) for v in g)
+        self.n_cells_total = sum(int(np.prod(gm.shape)) for gm in self.geoms)
+
+    @property
+    def n_parts(self) -> int:
+        n = _I32()
+        _check(load_library().lbm_batch_parts(self._h, ctypes.byref(n)), "lbm_batch_parts")
+        return n.value
+
+    def part_info(self, b: int) -> dict:
+        inf = lbm_geometry_info()
+        fo, co, po = _I64(), _I64(), _I64()
+        _check(load_library().lbm_batch_part_info(self._h, int(b), ctypes.byref(inf), ctypes.byref(fo),
+                                                  ctypes.byref(co), ctypes.byref(po)), "lbm_batch_part_info")
+        d = {k: getattr(inf, k) for k, _ in lbm_geometry_info._fields_}
+        d.update(fluid_offset=fo.value, cell_offset=co.value, plane_offset=po.value)
+        return d
+
+    def moments(self, rho=None, u=None):
+        import torch
+
+        dev = self.workspace.device
+        if rho is None:
+            rho = torch.empty(self.n_cells_total, dtype=torch.float32, device=dev)
+        if u is None:
+            u = torch.empty((3, self.n_cells_total), dtype=torch.float32, device=dev)
+        _check(load_library().lbm_moments(self._h, _dev_ptr(rho), _dev_ptr(u)), "lbm_moments")
+        return rho, u
+
+    def plane_average(self) -> np.ndarray:
+        nplanes = sum(gm.box.nz for gm in self.geoms)
+        out = np.zeros((nplanes, 3), np.float64)
+        _check(load_library().lbm_plane_average(self._h, _np_ptr(out)), "lbm_plane_average")
+        return out
+
+    def permeabilities(self) -> np.ndarray:
+        out = np.zeros(len(self.geoms), np.float64)
+        _check(load_library().lbm_batch_permeability(self._h, _np_ptr(out)), "lbm_batch_permeability")
+        return out
+
+    def profile_residuals(self) -> np.ndarray:
+        out = np.zeros(len(self.geoms), np.float64)
+        _check(load_library().lbm_batch_profile_residual(self._h, _np_ptr(out)), "lbm_batch_profile_residual")
+        return out
+
+
+def lbm_batch_init(geoms, **kw) -> BatchSolver:
+    return BatchSolver(geoms, **kw)
 
 
 def lbm_step(solver: Solver, n: int = 1):

@@ -1,4 +1,5 @@
 // lbm_api.cpp -- the extern "C" entry points declared in include/lbm.h.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -11,15 +12,26 @@ namespace lbm {
 
 int residual_partial_count(int64_t n_fluid);   // lbm_post.cu
 
-Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int storage, size_t n_bins,
-                   size_t n_images)
+Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size_t n_bins, size_t n_images)
 {
     Layout L{};
     const size_t A = 256;
-    const int64_t ncell = (int64_t)box.nx * box.ny * box.nz;
+    int64_t n_fluid = 0, n_links = 0, ncell_max = 0;
+    int32_t n_planes = 0, n_poff = 0;
+    for (const Geometry *g : geoms) {
+        n_fluid += g->n_fluid;
+        n_links += g->n_links;
+        ncell_max = std::max(ncell_max, g->ncell());
+        n_planes += g->box.nz;
+        n_poff += g->box.nz + 1;
+    }
+    const bool single = geoms.size() == 1;
+    const lbm_box &b0 = geoms[0]->box;
     const int64_t n_pad = ((n_fluid > 0 ? n_fluid : 1) + kBlock - 1) / kBlock * kBlock;
     L.n_pad = (int32_t)n_pad;
-    L.n_scan_blocks = (ncell + kBlock - 1) / kBlock;
+    L.n_parts = (int32_t)geoms.size();
+    L.n_planes = n_planes;
+    L.n_scan_blocks = (ncell_max + kBlock - 1) / kBlock;
     L.n_partials = residual_partial_count(n_fluid);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -28,10 +40,10 @@ Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int sto
         return at;
     };
     const size_t pdf_bytes = (size_t)kQ * n_pad * storage_bytes(storage);
-    const size_t build_bytes = align_up((size_t)ncell * 4, A) + align_up((size_t)ncell, A);
+    const size_t build_bytes = align_up((size_t)ncell_max * 4, A) + align_up((size_t)ncell_max, A);
     L.pdf = take(pdf_bytes > build_bytes ? pdf_bytes : build_bytes);
     L.idx_map = L.pdf;
-    L.mask = L.pdf + align_up((size_t)ncell * 4, A);
+    L.mask = L.pdf + align_up((size_t)ncell_max * 4, A);
     L.nbr = take((size_t)(kQ - 1) * n_pad * 4);
     L.lmask = take((size_t)n_pad * 4);
     L.warp_off = take((size_t)n_pad / 32 * 4);
@@ -39,18 +51,20 @@ Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int sto
     L.link_a = take((size_t)(n_links > 0 ? n_links : 1) * 4);
     L.link_q = take((size_t)(n_links > 0 ? n_links : 1) * 8);
     L.fluid_cell = take((size_t)n_pad * 4);
-    L.plane_off = take((size_t)(box.nz + 1) * 4);
-    L.row_words = take((size_t)box.ny * box.nz * ((box.nx + 31) / 32) * 8);
-    L.cell_xr = take((size_t)n_pad * 4);
+    L.plane_off = take((size_t)n_poff * 4);
+    L.row_words = take(single ? (size_t)b0.ny * b0.nz * ((b0.nx + 31) / 32) * 8 : 0);
+    L.cell_xr = take(single ? (size_t)n_pad * 4 : 0);
     L.u_cur = take((size_t)3 * n_pad * 4);
     L.u_prev = take((size_t)3 * n_pad * 4);
     L.rho_cur = take((size_t)n_pad * 4);
-    L.prof_prev = take((size_t)box.nz * 8);
+    L.prof_prev = take((size_t)n_planes * 8);
     L.bins_start = take((n_bins + 1) * 4);
     L.bins_img = take(n_images * sizeof(SphereImage));
     L.scan_tmp = take((size_t)(L.n_scan_blocks + 1) * 4);
     L.partials = take((size_t)L.n_partials * 3 * 8);
-    L.result = take((size_t)(3 * box.nz + 8) * 8);
+    L.result = take((res_part(L, L.n_parts) + 8) * 8);
+    L.part_shift = take((size_t)L.n_parts * 4);
+    L.part_foff = take((size_t)(L.n_parts + 1) * 4);
     L.total = off;
     return L;
 }
@@ -70,10 +84,15 @@ bool rows_packable(const lbm_box &box)
 
 // The kernels address populations with 32-bit element offsets (19 n_pad <
 // 2^32, about 226 million fluid cells) and links with 32-bit indices.
-static bool size_ok(const Geometry &g)
+static bool size_ok(const std::vector<const Geometry *> &geoms)
 {
-    const int64_t n_pad = (g.n_fluid + kBlock - 1) / kBlock * kBlock;
-    return (int64_t)kQ * n_pad < ((int64_t)1 << 32) && g.n_links <= (int64_t)std::numeric_limits<uint32_t>::max();
+    int64_t nf = 0, nl = 0;
+    for (const Geometry *g : geoms) {
+        nf += g->n_fluid;
+        nl += g->n_links;
+    }
+    const int64_t n_pad = (nf + kBlock - 1) / kBlock * kBlock;
+    return (int64_t)kQ * n_pad < ((int64_t)1 << 32) && nl <= (int64_t)std::numeric_limits<uint32_t>::max();
 }
 
 static bool params_ok(const lbm_params *p)
@@ -83,17 +102,141 @@ static bool params_ok(const lbm_params *p)
     if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return false;
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return false;
-    if (p->flags != 0 && p->flags != LBM_FLAG_NEIGHBOUR_TABLE && p->flags != LBM_FLAG_ROW_NEIGHBOURS) return false;
+    const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE;
+    if ((p->flags & ~known) != 0) return false;
+    if ((p->flags & LBM_FLAG_NEIGHBOUR_TABLE) && (p->flags & LBM_FLAG_ROW_NEIGHBOURS)) return false;
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
 }
 
-static int bins_for(const Geometry &g, Bins &bins)
+// Largest bin table over the parts (the device build uploads one part at a time).
+static int bins_extent(const std::vector<const Geometry *> &geoms, size_t &n_bins, size_t &n_images)
 {
+    n_bins = 0;
+    n_images = 0;
     try {
-        build_bins(g.box, g.spheres, bins);
+        for (const Geometry *g : geoms) {
+            Bins bins;
+            build_bins(g->box, g->spheres, bins);
+            n_bins = std::max(n_bins, bins.start.size() - 1);
+            n_images = std::max(n_images, bins.images.size());
+        }
     } catch (const std::bad_alloc &) {
         return LBM_ENOMEM;
     }
+    return LBM_OK;
+}
+
+static int collect(const lbm_geometry *const *geoms, int32_t n, std::vector<const Geometry *> &out)
+{
+    if (!geoms || n < 1) return LBM_EINVAL;
+    out.clear();
+    for (int32_t b = 0; b < n; ++b) {
+        if (!geoms[b]) return LBM_EINVAL;
+        out.push_back(geoms[b]);
+    }
+    return LBM_OK;
+}
+
+static int workspace_size(const std::vector<const Geometry *> &geoms, const lbm_params *params, size_t *bytes)
+{
+    if (!bytes || !params_ok(params) || !size_ok(geoms)) return LBM_EINVAL;
+    size_t nb = 0, ni = 0;
+    const int rc = bins_extent(geoms, nb, ni);
+    if (rc != LBM_OK) return rc;
+    *bytes = make_layout(geoms, params->storage, nb, ni).total;
+    return LBM_OK;
+}
+
+static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_params *params, void *dev_workspace,
+                      size_t bytes, const float *dev_u0, void *stream, lbm_solver **out)
+{
+    if (!out || !params_ok(params)) return LBM_EINVAL;
+    *out = nullptr;
+    if (!size_ok(geoms)) return LBM_EINVAL;
+    if (!dev_workspace || ((uintptr_t)dev_workspace & 255u) != 0) return LBM_ESIZE;
+    size_t nb = 0, ni = 0;
+    int rc = bins_extent(geoms, nb, ni);
+    if (rc != LBM_OK) return rc;
+    const Layout L = make_layout(geoms, params->storage, nb, ni);
+    if (bytes < L.total) return LBM_ESIZE;
+    lbm_solver *s = new (std::nothrow) lbm_solver();
+    if (!s) return LBM_ENOMEM;
+    s->box = geoms[0]->box;
+    s->params = *params;
+    s->stream = (cudaStream_t)stream;
+    s->ws = (char *)dev_workspace;
+    s->lay = L;
+    int64_t cell_base = 0;
+    int32_t fluid_off = 0, plane_base = 0, poff_base = 0;
+    for (const Geometry *g : geoms) {
+        Part P;
+        P.box = g->box;
+        P.cell_base = cell_base;
+        P.n_cells = g->ncell();
+        P.fluid_off = fluid_off;
+        P.n_fluid = (int32_t)g->n_fluid;
+        P.n_links = g->n_links;
+        P.n_spheres = (int64_t)(g->spheres.size() / 4);
+        P.plane_base = plane_base;
+        P.poff_base = poff_base;
+        s->parts.push_back(P);
+        cell_base += P.n_cells;
+        fluid_off += P.n_fluid;
+        plane_base += g->box.nz;
+        poff_base += g->box.nz + 1;
+        s->n_links += g->n_links;
+        s->n_spheres += P.n_spheres;
+    }
+    s->n_cells = cell_base;
+    s->n_fluid = fluid_off;
+    s->n_pad = L.n_pad;
+    s->shift_host.assign(s->parts.size(), 0.0f);
+    s->nu = (params->tau - 0.5) / 3.0;
+    s->omega_p = 1.0 / params->tau;
+    s->omega_m = 1.0 / (params->lambda / (params->tau - 0.5) + 0.5);
+    s->pdf = s->ws + L.pdf;
+    s->nbr = (int32_t *)(s->ws + L.nbr);
+    s->lmask = (uint32_t *)(s->ws + L.lmask);
+    s->warp_off = (uint32_t *)(s->ws + L.warp_off);
+    s->link_a = (float *)(s->ws + L.link_a);
+    s->link_q = (double *)(s->ws + L.link_q);
+    s->fluid_cell = (int32_t *)(s->ws + L.fluid_cell);
+    s->plane_off = (int32_t *)(s->ws + L.plane_off);
+    s->row_words = (uint2 *)(s->ws + L.row_words);
+    s->cell_xr = (uint32_t *)(s->ws + L.cell_xr);
+    s->u_cur = (float *)(s->ws + L.u_cur);
+    s->u_prev = (float *)(s->ws + L.u_prev);
+    s->rho_cur = (float *)(s->ws + L.rho_cur);
+    s->prof_prev = (double *)(s->ws + L.prof_prev);
+    s->partials = (double *)(s->ws + L.partials);
+    s->result = (double *)(s->ws + L.result);
+    s->part_shift = (float *)(s->ws + L.part_shift);
+    s->part_foff = (int32_t *)(s->ws + L.part_foff);
+    const bool single = geoms.size() == 1;
+    s->n_words = (s->box.nx + 31) / 32;
+    s->x_bits = x_bits_for(s->box.nx);
+    {
+        bool rows = params->storage != LBM_F32;   // auto: see LBM_FLAG_* in lbm.h
+        if (params->flags & LBM_FLAG_NEIGHBOUR_TABLE) rows = false;
+        if (params->flags & LBM_FLAG_ROW_NEIGHBOURS) rows = true;
+        s->odd_rows = rows && single && rows_packable(s->box);
+    }
+    s->use_graph = !(params->flags & LBM_FLAG_NO_GRAPH);
+    s->autotune = !(params->flags & LBM_FLAG_NO_AUTOTUNE);
+    std::vector<int32_t> foff;
+    for (const Part &P : s->parts) foff.push_back(P.fluid_off);
+    foff.push_back(s->n_fluid);
+    rc = device_build(*s, geoms);
+    if (rc == LBM_OK && cudaMemcpyAsync(s->part_foff, foff.data(), foff.size() * 4, cudaMemcpyHostToDevice,
+                                        s->stream) != cudaSuccess)
+        rc = LBM_ECUDA;
+    if (rc == LBM_OK) rc = launch_init(*s, dev_u0);
+    if (rc == LBM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LBM_ECUDA;
+    if (rc != LBM_OK) {
+        delete s;
+        return rc;
+    }
+    *out = s;
     return LBM_OK;
 }
 
@@ -178,79 +321,70 @@ void lbm_geometry_destroy(lbm_geometry *g) { delete g; }
 
 int lbm_workspace_size(const lbm_geometry *g, const lbm_params *params, size_t *bytes)
 {
-    if (!g || !bytes || !params_ok(params)) return LBM_EINVAL;
-    if (!size_ok(*g)) return LBM_EINVAL;
-    Bins bins;
-    const int rc = bins_for(*g, bins);
-    if (rc != LBM_OK) return rc;
-    *bytes = make_layout(g->box, g->n_fluid, g->n_links, params->storage, bins.start.size() - 1,
-                         bins.images.size()).total;
-    return LBM_OK;
+    if (!g) return LBM_EINVAL;
+    return workspace_size({g}, params, bytes);
 }
 
 int lbm_init(const lbm_geometry *g, const lbm_params *params, void *dev_workspace, size_t bytes,
              const float *dev_u0, void *stream, lbm_solver **out)
 {
-    if (!g || !out || !params_ok(params)) return LBM_EINVAL;
-    *out = nullptr;
-    if (!size_ok(*g)) return LBM_EINVAL;
-    if (!dev_workspace || ((uintptr_t)dev_workspace & 255u) != 0) return LBM_ESIZE;
-    Bins bins;
-    int rc = bins_for(*g, bins);
-    if (rc != LBM_OK) return rc;
-    const Layout L = make_layout(g->box, g->n_fluid, g->n_links, params->storage, bins.start.size() - 1,
-                                 bins.images.size());
-    if (bytes < L.total) return LBM_ESIZE;
-    lbm_solver *s = new (std::nothrow) lbm_solver();
-    if (!s) return LBM_ENOMEM;
-    s->box = g->box;
-    s->params = *params;
-    s->stream = (cudaStream_t)stream;
-    s->ws = (char *)dev_workspace;
-    s->lay = L;
-    s->n_cells = g->ncell();
-    s->n_fluid = (int32_t)g->n_fluid;
-    s->n_pad = L.n_pad;
-    s->n_links = g->n_links;
-    s->n_spheres = (int64_t)(g->spheres.size() / 4);
-    s->nu = (params->tau - 0.5) / 3.0;
-    s->omega_p = 1.0 / params->tau;
-    s->omega_m = 1.0 / (params->lambda / (params->tau - 0.5) + 0.5);
-    s->pdf = s->ws + L.pdf;
-    s->nbr = (int32_t *)(s->ws + L.nbr);
-    s->lmask = (uint32_t *)(s->ws + L.lmask);
-    s->warp_off = (uint32_t *)(s->ws + L.warp_off);
-    s->link_a = (float *)(s->ws + L.link_a);
-    s->link_q = (double *)(s->ws + L.link_q);
-    s->fluid_cell = (int32_t *)(s->ws + L.fluid_cell);
-    s->plane_off = (int32_t *)(s->ws + L.plane_off);
-    s->row_words = (uint2 *)(s->ws + L.row_words);
-    s->cell_xr = (uint32_t *)(s->ws + L.cell_xr);
-    s->n_words = (g->box.nx + 31) / 32;
-    s->x_bits = x_bits_for(g->box.nx);
-    {
-        bool rows = params->storage != LBM_F32;   // auto: see LBM_FLAG_* in lbm.h
-        if (params->flags == LBM_FLAG_NEIGHBOUR_TABLE) rows = false;
-        if (params->flags == LBM_FLAG_ROW_NEIGHBOURS) rows = true;
-        s->odd_rows = rows && rows_packable(g->box);
+    if (!g) return LBM_EINVAL;
+    return init_parts({g}, params, dev_workspace, bytes, dev_u0, stream, out);
+}
+
+int lbm_batch_workspace_size(const lbm_geometry *const *geoms, int32_t n, const lbm_params *params, size_t *bytes)
+{
+    std::vector<const Geometry *> v;
+    const int rc = collect(geoms, n, v);
+    return rc != LBM_OK ? rc : workspace_size(v, params, bytes);
+}
+
+int lbm_batch_init(const lbm_geometry *const *geoms, int32_t n, const lbm_params *params, void *dev_workspace,
+                   size_t bytes, const float *dev_u0, void *stream, lbm_solver **out)
+{
+    std::vector<const Geometry *> v;
+    const int rc = collect(geoms, n, v);
+    return rc != LBM_OK ? rc : init_parts(v, params, dev_workspace, bytes, dev_u0, stream, out);
+}
+
+int lbm_batch_parts(const lbm_solver *s, int32_t *n_parts)
+{
+    if (!s || !n_parts) return LBM_EINVAL;
+    *n_parts = (int32_t)s->parts.size();
+    return LBM_OK;
+}
+
+int lbm_batch_part_info(const lbm_solver *s, int32_t part, lbm_geometry_info *info, int64_t *fluid_offset,
+                        int64_t *cell_offset, int64_t *plane_offset)
+{
+    if (!s || part < 0 || part >= (int32_t)s->parts.size()) return LBM_EINVAL;
+    const Part &P = s->parts[part];
+    if (info) {
+        info->n_cells = P.n_cells;
+        info->n_fluid = P.n_fluid;
+        info->n_links = P.n_links;
+        info->n_spheres = P.n_spheres;
+        info->porosity = (double)P.n_fluid / (double)P.n_cells;
     }
-    s->u_cur = (float *)(s->ws + L.u_cur);
-    s->u_prev = (float *)(s->ws + L.u_prev);
-    s->rho_cur = (float *)(s->ws + L.rho_cur);
-    s->prof_prev = (double *)(s->ws + L.prof_prev);
-    s->partials = (double *)(s->ws + L.partials);
-    s->result = (double *)(s->ws + L.result);
-    s->nbins_x = bins.nbx;
-    s->nbins_y = bins.nby;
-    s->nbins_z = bins.nbz;
-    rc = device_build(*s, *g, bins);
-    if (rc == LBM_OK) rc = launch_init(*s, dev_u0);
-    if (rc == LBM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LBM_ECUDA;
-    if (rc != LBM_OK) {
-        delete s;
-        return rc;
+    if (fluid_offset) *fluid_offset = P.fluid_off;
+    if (cell_offset) *cell_offset = P.cell_base;
+    if (plane_offset) *plane_offset = P.plane_base;
+    return LBM_OK;
+}
+
+int lbm_batch_permeability(lbm_solver *s, double *k_out)
+{
+    if (!s || !k_out || s->params.g[0] == 0.0) return LBM_EINVAL;
+    for (int b = 0; b < (int)s->parts.size(); ++b) {
+        const int rc = launch_permeability(*s, b, 0, s->parts[b].box.nz - 1);
+        if (rc != LBM_OK) return rc;
     }
-    *out = s;
+    std::vector<double> r(8 * s->parts.size());
+    if (cudaMemcpyAsync(r.data(), s->result + res_part(s->lay, 0), r.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+    for (size_t b = 0; b < s->parts.size(); ++b) k_out[b] = r[8 * b];
     return LBM_OK;
 }
 
@@ -258,7 +392,7 @@ int lbm_reset(lbm_solver *s, const float *dev_u0)
 {
     if (!s) return LBM_EINVAL;
     s->has_prev = false;
-    s->has_prev_profile = false;
+    for (Part &P : s->parts) P.has_prev_profile = false;
     return launch_init(*s, dev_u0);
 }
 
@@ -279,7 +413,7 @@ int lbm_plane_average(lbm_solver *s, double *host_out)
     if (!s || !host_out) return LBM_EINVAL;
     int rc = launch_plane_average(*s);
     if (rc != LBM_OK) return rc;
-    if (cudaMemcpyAsync(host_out, s->result, sizeof(double) * 3 * (size_t)s->box.nz, cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(host_out, s->result, sizeof(double) * 3 * (size_t)s->lay.n_planes, cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess)
         return LBM_ECUDA;
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
@@ -287,16 +421,16 @@ int lbm_plane_average(lbm_solver *s, double *host_out)
 
 int lbm_permeability(lbm_solver *s, int32_t z_lo, int32_t z_hi, double *k_out)
 {
-    if (!s || !k_out) return LBM_EINVAL;
+    if (!s || !k_out || s->parts.size() != 1) return LBM_EINVAL;
     if (z_lo == -1 && z_hi == -1) {
         z_lo = 0;
         z_hi = s->box.nz - 1;
     }
     if (z_lo < 0 || z_hi >= s->box.nz || z_lo > z_hi || s->params.g[0] == 0.0) return LBM_EINVAL;
-    int rc = launch_permeability(*s, z_lo, z_hi);
+    int rc = launch_permeability(*s, 0, z_lo, z_hi);
     if (rc != LBM_OK) return rc;
-    if (cudaMemcpyAsync(k_out, s->result + 3 * (size_t)s->box.nz, sizeof(double), cudaMemcpyDeviceToHost,
-                        s->stream) != cudaSuccess)
+    if (cudaMemcpyAsync(k_out, s->result + res_part(s->lay, 0), sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
         return LBM_ECUDA;
     return cudaStreamSynchronize(s->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
@@ -307,7 +441,9 @@ int lbm_residual(lbm_solver *s, double *res_out)
     int rc = launch_residual(*s);
     if (rc != LBM_OK) return rc;
     double r[3];
-    if (cudaMemcpyAsync(r, s->result, sizeof(r), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) return LBM_ECUDA;
+    if (cudaMemcpyAsync(r, s->result + res_field(s->lay), sizeof(r), cudaMemcpyDeviceToHost, s->stream) !=
+        cudaSuccess)
+        return LBM_ECUDA;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
     const bool had_prev = s->has_prev;
     std::swap(s->u_cur, s->u_prev);
@@ -320,52 +456,96 @@ int lbm_residual(lbm_solver *s, double *res_out)
     return LBM_OK;
 }
 
+// Per-part profile residuals (host array of n_parts); the largest is returned.
+static int profile_residuals(lbm_solver *s, double *per_part, double *worst)
+{
+    int rc = launch_profile_residual(*s);
+    if (rc != LBM_OK) return rc;
+    std::vector<double> r(8 * s->parts.size());
+    if (cudaMemcpyAsync(r.data(), s->result + res_part(s->lay, 0), r.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+    double w = 0.0;
+    bool bad = false;
+    for (size_t b = 0; b < s->parts.size(); ++b) {
+        Part &P = s->parts[b];
+        const double num = r[8 * b + 1], den = r[8 * b + 2];
+        bad |= r[8 * b + 3] != 0.0 || !std::isfinite(num) || !std::isfinite(den);
+        double v = std::numeric_limits<double>::infinity();
+        if (P.has_prev_profile) v = den > 0.0 ? std::sqrt(num) / std::sqrt(den) : (num > 0.0 ? v : 0.0);
+        P.has_prev_profile = true;
+        if (per_part) per_part[b] = v;
+        w = std::max(w, v);
+    }
+    if (bad) {
+        *worst = std::numeric_limits<double>::quiet_NaN();
+        return LBM_ENAN;
+    }
+    *worst = w;
+    return LBM_OK;
+}
+
 int lbm_profile_residual(lbm_solver *s, double *res_out)
 {
     if (!s || !res_out) return LBM_EINVAL;
-    int rc = launch_profile_residual(*s);
+    return profile_residuals(s, nullptr, res_out);
+}
+
+int lbm_batch_profile_residual(lbm_solver *s, double *res_out)
+{
+    if (!s || !res_out) return LBM_EINVAL;
+    double worst;
+    return profile_residuals(s, res_out, &worst);
+}
+
+// Mean density deviation per part (host array) and over the whole solver.
+static int part_masses(lbm_solver *s, std::vector<double> &per_part, double *mean_all)
+{
+    per_part.assign(s->parts.size(), 0.0);
+    *mean_all = 0.0;
+    if (s->n_fluid == 0) return LBM_OK;
+    int rc = launch_mass(*s);
     if (rc != LBM_OK) return rc;
-    double r[3];
-    if (cudaMemcpyAsync(r, s->result + 3 * (size_t)s->box.nz + 1, sizeof(r), cudaMemcpyDeviceToHost, s->stream) !=
-        cudaSuccess)
+    std::vector<double> r(8 * s->parts.size());
+    double g[2];
+    if (cudaMemcpyAsync(r.data(), s->result + res_part(s->lay, 0), r.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(g, s->result + res_mass(s->lay), sizeof(g), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
         return LBM_ECUDA;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
-    const bool had_prev = s->has_prev_profile;
-    s->has_prev_profile = true;
-    if (r[2] != 0.0 || !std::isfinite(r[0]) || !std::isfinite(r[1])) {
-        *res_out = std::numeric_limits<double>::quiet_NaN();
-        return LBM_ENAN;
+    bool bad = g[1] != 0.0 || !std::isfinite(g[0]);
+    for (size_t b = 0; b < s->parts.size(); ++b) {
+        bad |= r[8 * b + 5] != 0.0 || !std::isfinite(r[8 * b + 4]);
+        per_part[b] = s->parts[b].n_fluid ? r[8 * b + 4] / (double)s->parts[b].n_fluid : 0.0;
     }
-    *res_out = had_prev ? std::sqrt(r[0]) / std::sqrt(r[1]) : std::numeric_limits<double>::infinity();
+    if (bad) return LBM_ENAN;
+    *mean_all = g[0] / (double)s->n_fluid;
     return LBM_OK;
 }
 
 int lbm_mass(lbm_solver *s, double *mean_drho)
 {
     if (!s || !mean_drho) return LBM_EINVAL;
-    if (s->n_fluid == 0) {
-        *mean_drho = 0.0;
-        return LBM_OK;
-    }
-    int rc = launch_mass(*s);
-    if (rc != LBM_OK) return rc;
-    double r[2];
-    if (cudaMemcpyAsync(r, s->result + 3 * (size_t)s->box.nz + 4, sizeof(r), cudaMemcpyDeviceToHost, s->stream) !=
-        cudaSuccess)
-        return LBM_ECUDA;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
-    if (r[1] != 0.0 || !std::isfinite(r[0])) return LBM_ENAN;
-    *mean_drho = r[0] / (double)s->n_fluid;
-    return LBM_OK;
+    std::vector<double> per;
+    return part_masses(s, per, mean_drho);
 }
 
 int lbm_recenter(lbm_solver *s, double *shift_out)
 {
-    double m = 0.0;
-    int rc = lbm_mass(s, &m);
+    if (!s) return LBM_EINVAL;
+    std::vector<double> per;
+    double all = 0.0;
+    int rc = part_masses(s, per, &all);
     if (rc != LBM_OK) return rc;
-    s->drho_shift = m;   // the state is measured afresh: replace, do not accumulate
-    if (shift_out) *shift_out = s->drho_shift;
+    // the state is measured afresh: replace any pending shift, do not accumulate
+    for (size_t b = 0; b < per.size(); ++b) s->shift_host[b] = (float)per[b];
+    if (cudaMemcpyAsync(s->part_shift, s->shift_host.data(), sizeof(float) * per.size(), cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    s->shift_pending = true;
+    if (shift_out) *shift_out = all;
     return LBM_OK;
 }
 

@@ -1,15 +1,18 @@
 // lbm_build.cu -- device construction of the sparse fluid list, the neighbour
 // table and the wall-link list with the link fractions q of Eq. (CLI).
 //
-// Steps (all on the solver's stream):
+// Steps (all on the solver's stream), for each part (independent box) in turn:
 //   1. per block of cells: count fluid cells of the uploaded solid mask;
 //      exclusive scan of the block counts;
-//   2. dense index map cell -> fluid index (-1 solid) and fluid_cell[];
+//   2. dense index map cell -> global fluid index (-1 solid) and fluid_cell[]
+//      (concatenated cell index);
 //   3. neighbour table nbr[k][i] and link mask lmask[i] (bit k: x + e_k solid),
-//      link counts per aligned group of 32 fluid cells; exclusive scan;
-//   4. link fraction q and CLI coefficient a = (1-2q)/(1+2q) per link
-//      (a = 0, bounce-back, when the second node x - e_k is solid);
-//   5. first fluid index of each z plane.
+//      packed (x, row) and row bitmask words (single part only);
+//   4. first fluid index of each z plane of the part;
+// then over the whole solver: link counts per aligned group of 32 fluid cells
+// and their exclusive scan; and again per part:
+//   5. link fraction q and CLI coefficient a = (1-2q)/(1+2q) per link
+//      (a = 0, bounce-back, when the second node x - e_k is solid).
 // The index map and the mask live in the population region, which is written
 // only afterwards by the initialisation.
 #include <cstdio>
@@ -72,8 +75,8 @@ __global__ void k_scan_exclusive(uint32_t *__restrict__ v, int64_t n, uint32_t *
 
 // 2. index map and fluid list (fluid cells keep increasing cell order)
 __global__ void k_fill_index(const uint8_t *__restrict__ mask, int64_t ncell,
-                             const uint32_t *__restrict__ block_off, int32_t *__restrict__ idx_map,
-                             int32_t *__restrict__ fluid_cell)
+                             const uint32_t *__restrict__ block_off, int32_t fluid_off, int64_t cell_base,
+                             int32_t *__restrict__ idx_map, int32_t *__restrict__ fluid_cell)
 {
     __shared__ uint32_t warp_cnt[kBlock / 32];
     const int64_t c = (int64_t)blockIdx.x * kBlock + threadIdx.x;
@@ -86,9 +89,9 @@ __global__ void k_fill_index(const uint8_t *__restrict__ mask, int64_t ncell,
     for (int w = 0; w < warp; ++w) before += warp_cnt[w];
     before += __popc(ballot & ((1u << lane) - 1u));
     if (c < ncell) {
-        const int32_t idx = fluid ? (int32_t)(block_off[blockIdx.x] + before) : -1;
+        const int32_t idx = fluid ? fluid_off + (int32_t)(block_off[blockIdx.x] + before) : -1;
         idx_map[c] = idx;
-        if (fluid) fluid_cell[idx] = (int32_t)c;
+        if (fluid) fluid_cell[idx] = (int32_t)(cell_base + c);
     }
 }
 
@@ -115,35 +118,49 @@ __global__ void k_row_words(const int32_t *__restrict__ idx_map, int nx, int64_t
     words[t] = make_uint2(bits, base);
 }
 
-// 3. neighbour table, link mask, link count per aligned group of 32 cells,
-//    packed (x, row) of each fluid cell
+// 3. neighbour table, link mask and packed (x, row) of the fluid cells of one
+//    part; idx_map holds global fluid indices.
 __global__ void k_neighbours(const int32_t *__restrict__ idx_map, const int32_t *__restrict__ fluid_cell,
-                             int32_t n_fluid, int32_t n_pad, int nx, int ny, int nz, int periodic_z,
-                             int x_bits, int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
-                             uint32_t *__restrict__ warp_cnt, uint32_t *__restrict__ cell_xr)
+                             int32_t begin, int32_t end, int64_t cell_base, int32_t n_pad, int nx, int ny, int nz,
+                             int periodic_z, int x_bits, int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
+                             uint32_t *__restrict__ cell_xr)
+{
+    const int32_t i = begin + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
+    if (i >= end) return;
+    const int32_t c = (int32_t)(fluid_cell[i] - cell_base);
+    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+    if (cell_xr) cell_xr[i] = (uint32_t)x | ((uint32_t)(c / nx) << x_bits);
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) {
+        const int xn = wrap(x + ex(k), nx), yn = wrap(y + ey(k), ny);
+        int zn = z + ez(k);
+        int32_t j = -1;
+        if (periodic_z) zn = wrap(zn, nz);
+        if (zn >= 0 && zn < nz) j = idx_map[xn + nx * (yn + ny * zn)];
+        nbr[(size_t)(k - 1) * n_pad + i] = j;
+        m |= (uint32_t)(j < 0) << k;
+    }
+    lmask[i] = m;
+}
+
+// Padding cells beyond the last fluid cell: no links, neighbours -1.
+__global__ void k_pad_cells(int32_t n_fluid, int32_t n_pad, int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
+                            int32_t *__restrict__ fluid_cell, uint32_t *__restrict__ cell_xr)
+{
+    const int32_t i = n_fluid + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
+    if (i >= n_pad) return;
+    for (int k = 1; k < kQ; ++k) nbr[(size_t)(k - 1) * n_pad + i] = -1;
+    lmask[i] = 0;
+    fluid_cell[i] = 0;
+    if (cell_xr) cell_xr[i] = 0;
+}
+
+// Link counts per aligned group of 32 fluid cells.
+__global__ void k_warp_counts(const uint32_t *__restrict__ lmask, uint32_t *__restrict__ warp_cnt)
 {
     const int32_t i = blockIdx.x * kBlock + threadIdx.x;
-    uint32_t m = 0;
-    if (i < n_fluid) {
-        const int32_t c = fluid_cell[i];
-        const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
-        cell_xr[i] = (uint32_t)x | ((uint32_t)(c / nx) << x_bits);
-#pragma unroll
-        for (int k = 1; k < kQ; ++k) {
-            const int xn = wrap(x + ex(k), nx), yn = wrap(y + ey(k), ny);
-            int zn = z + ez(k);
-            int32_t j = -1;
-            if (periodic_z) zn = wrap(zn, nz);
-            if (zn >= 0 && zn < nz) j = idx_map[xn + nx * (yn + ny * zn)];
-            nbr[(size_t)(k - 1) * n_pad + i] = j;
-            m |= (uint32_t)(j < 0) << k;
-        }
-    } else if (i < n_pad) {
-        for (int k = 1; k < kQ; ++k) nbr[(size_t)(k - 1) * n_pad + i] = -1;
-        cell_xr[i] = 0;
-    }
-    if (i < n_pad) lmask[i] = m;
-    uint32_t cnt = __popc(m);
+    uint32_t cnt = __popc(lmask[i]);
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
     if ((threadIdx.x & 31) == 0) warp_cnt[i >> 5] = cnt;
 }
@@ -173,16 +190,19 @@ struct LinkArgs {
     const SphereImage *images;
     float *link_a;
     double *link_q;
-    int32_t n_fluid;
+    int32_t begin, end, n_fluid;
+    int64_t cell_base;
     int nx, ny, nz, periodic_z;
     int nbx, nby;
     double q_lo, q_hi;
 };
 
-// 4. link fractions and CLI coefficients
+// 5. link fractions and CLI coefficients of the cells of one part.  The grid
+// covers the aligned groups of 32 that contain the part, so the warp prefix
+// sum of link counts sees every cell of each group.
 __global__ void k_links(LinkArgs a)
 {
-    const int32_t i = blockIdx.x * kBlock + threadIdx.x;
+    const int32_t i = (a.begin & ~31) + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
     const uint32_t m = i < a.n_fluid ? a.lmask[i] : 0u;
     const uint32_t cnt = __popc(m);
     uint32_t incl = cnt;
@@ -191,9 +211,9 @@ __global__ void k_links(LinkArgs a)
         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += y;
     }
-    if (i >= a.n_fluid || m == 0) return;
+    if (i < a.begin || i >= a.end || m == 0) return;
     uint32_t off = a.warp_off[i >> 5] + incl - cnt;
-    const int32_t c = a.fluid_cell[i];
+    const int32_t c = (int32_t)(a.fluid_cell[i] - a.cell_base);
     const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
     const int bin = x / kBinEdge + a.nbx * (y / kBinEdge + a.nby * (z / kBinEdge));
     const int b0 = a.bin_start[bin], b1 = a.bin_start[bin + 1];
@@ -225,17 +245,17 @@ __global__ void k_links(LinkArgs a)
     }
 }
 
-// 5. first fluid index of each z plane (plane_off[nz] = n_fluid)
-__global__ void k_plane_offsets(const int32_t *__restrict__ fluid_cell, int32_t n_fluid, int plane, int nz,
-                                int32_t *__restrict__ plane_off)
+// 4. first fluid index of each z plane of one part (plane_off[nz] = end)
+__global__ void k_plane_offsets(const int32_t *__restrict__ fluid_cell, int32_t begin, int32_t end,
+                                int64_t cell_base, int plane, int nz, int32_t *__restrict__ plane_off)
 {
-    const int32_t i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= n_fluid) return;
-    const int z = fluid_cell[i] / plane;
-    const int zp = i == 0 ? -1 : fluid_cell[i - 1] / plane;
+    const int32_t i = begin + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
+    if (i >= end) return;
+    const int z = (int)((fluid_cell[i] - cell_base) / plane);
+    const int zp = i == begin ? -1 : (int)((fluid_cell[i - 1] - cell_base) / plane);
     for (int zz = zp + 1; zz <= z; ++zz) plane_off[zz] = i;
-    if (i == n_fluid - 1)
-        for (int zz = z + 1; zz <= nz; ++zz) plane_off[zz] = n_fluid;
+    if (i == end - 1)
+        for (int zz = z + 1; zz <= nz; ++zz) plane_off[zz] = end;
 }
 
 }  // namespace
@@ -245,12 +265,12 @@ __global__ void k_plane_offsets(const int32_t *__restrict__ fluid_cell, int32_t 
         if ((x) != cudaSuccess) return LBM_ECUDA;           \
     } while (0)
 
-int device_build(Solver &s, const Geometry &g, const Bins &bins)
+static unsigned blocks_for(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
 {
     const Layout &L = s.lay;
     cudaStream_t st = s.stream;
-    const int64_t ncell = s.n_cells;
-    const int nx = s.box.nx, ny = s.box.ny, nz = s.box.nz;
     uint8_t *d_mask = (uint8_t *)(s.ws + L.mask);
     int32_t *d_idx = (int32_t *)(s.ws + L.idx_map);
     uint32_t *d_scan = (uint32_t *)(s.ws + L.scan_tmp);
@@ -258,49 +278,82 @@ int device_build(Solver &s, const Geometry &g, const Bins &bins)
     uint32_t *d_total = (uint32_t *)(s.ws + L.result);
     int32_t *d_bstart = (int32_t *)(s.ws + L.bins_start);
     SphereImage *d_img = (SphereImage *)(s.ws + L.bins_img);
+    const bool single = s.parts.size() == 1;
+    uint32_t *cell_xr = single ? s.cell_xr : nullptr;
+    std::vector<uint32_t> counts(s.parts.size() + 1, 0);
 
-    LBM_CUDA_TRY(cudaMemcpyAsync(d_mask, g.mask.data(), (size_t)ncell, cudaMemcpyHostToDevice, st));
-    LBM_CUDA_TRY(cudaMemcpyAsync(d_bstart, bins.start.data(), bins.start.size() * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, st));
-    if (!bins.images.empty())
-        LBM_CUDA_TRY(cudaMemcpyAsync(d_img, bins.images.data(), bins.images.size() * sizeof(SphereImage),
-                                     cudaMemcpyHostToDevice, st));
-
-    const int64_t nblk = (ncell + kBlock - 1) / kBlock;
-    k_count_fluid<<<(unsigned)nblk, kBlock, 0, st>>>(d_mask, ncell, d_scan);
-    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(d_scan, nblk, d_total);
-    k_fill_index<<<(unsigned)nblk, kBlock, 0, st>>>(d_mask, ncell, d_scan, d_idx, s.fluid_cell);
-    LBM_CUDA_TRY(cudaGetLastError());
-
-    const unsigned fblk = (unsigned)(s.n_pad / kBlock);
-    if (s.n_pad > s.n_fluid)
-        LBM_CUDA_TRY(cudaMemsetAsync(s.fluid_cell + s.n_fluid, 0, sizeof(int32_t) * (s.n_pad - s.n_fluid), st));
-    k_neighbours<<<fblk, kBlock, 0, st>>>(d_idx, s.fluid_cell, s.n_fluid, s.n_pad, nx, ny, nz,
-                                          s.box.periodic_z, s.x_bits, s.nbr, s.lmask, d_wcnt, s.cell_xr);
-    {
-        const int64_t nrows = (int64_t)ny * nz, nwords = nrows * s.n_words;
-        k_row_words<<<(unsigned)((nwords + kBlock - 1) / kBlock), kBlock, 0, st>>>(d_idx, nx, nrows, s.n_words,
-                                                                                  s.row_words);
+    for (size_t b = 0; b < s.parts.size(); ++b) {
+        const Part &P = s.parts[b];
+        const Geometry &g = *geoms[b];
+        const int nx = P.box.nx, ny = P.box.ny, nz = P.box.nz;
+        const int64_t ncell = P.n_cells;
+        LBM_CUDA_TRY(cudaMemcpyAsync(d_mask, g.mask.data(), (size_t)ncell, cudaMemcpyHostToDevice, st));
+        const int64_t nblk = (ncell + kBlock - 1) / kBlock;
+        k_count_fluid<<<(unsigned)nblk, kBlock, 0, st>>>(d_mask, ncell, d_scan);
+        k_scan_exclusive<<<1, kScanThreads, 0, st>>>(d_scan, nblk, d_total + b);
+        k_fill_index<<<(unsigned)nblk, kBlock, 0, st>>>(d_mask, ncell, d_scan, P.fluid_off, P.cell_base, d_idx,
+                                                         s.fluid_cell);
+        LBM_CUDA_TRY(cudaGetLastError());
+        if (P.n_fluid > 0) {
+            const int32_t begin = P.fluid_off, end = P.fluid_off + P.n_fluid;
+            k_neighbours<<<blocks_for(P.n_fluid), kBlock, 0, st>>>(d_idx, s.fluid_cell, begin, end, P.cell_base,
+                                                                    s.n_pad, nx, ny, nz, P.box.periodic_z, s.x_bits,
+                                                                    s.nbr, s.lmask, cell_xr);
+            k_plane_offsets<<<blocks_for(P.n_fluid), kBlock, 0, st>>>(s.fluid_cell, begin, end, P.cell_base, nx * ny,
+                                                                       nz, s.plane_off + P.poff_base);
+        } else {
+            LBM_CUDA_TRY(cudaMemsetAsync(s.plane_off + P.poff_base, 0, sizeof(int32_t) * (nz + 1), st));
+        }
+        if (single) {
+            const int64_t nrows = (int64_t)ny * nz, nwords = nrows * s.n_words;
+            k_row_words<<<blocks_for(nwords), kBlock, 0, st>>>(d_idx, nx, nrows, s.n_words, s.row_words);
+        }
+        LBM_CUDA_TRY(cudaGetLastError());
+        // the next part reuses the mask and index map: keep the order
     }
+    if (s.n_pad > s.n_fluid)
+        k_pad_cells<<<blocks_for(s.n_pad - s.n_fluid), kBlock, 0, st>>>(s.n_fluid, s.n_pad, s.nbr, s.lmask,
+                                                                          s.fluid_cell, cell_xr);
+    k_warp_counts<<<(unsigned)(s.n_pad / kBlock), kBlock, 0, st>>>(s.lmask, d_wcnt);
     LBM_CUDA_TRY(cudaMemcpyAsync(s.warp_off, d_wcnt, sizeof(uint32_t) * (s.n_pad / 32), cudaMemcpyDeviceToDevice, st));
-    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(s.warp_off, s.n_pad / 32, d_total + 1);
+    k_scan_exclusive<<<1, kScanThreads, 0, st>>>(s.warp_off, s.n_pad / 32, d_total + s.parts.size());
     LBM_CUDA_TRY(cudaGetLastError());
 
-    LinkArgs la{s.fluid_cell, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, s.n_fluid,
-                nx, ny, nz, s.box.periodic_z, bins.nbx, bins.nby, s.box.q_lo, s.box.q_hi};
-    k_links<<<fblk, kBlock, 0, st>>>(la);
-    LBM_CUDA_TRY(cudaMemsetAsync(s.plane_off, 0, sizeof(int32_t) * (nz + 1), st));
-    if (s.n_fluid > 0)
-        k_plane_offsets<<<(unsigned)((s.n_fluid + kBlock - 1) / kBlock), kBlock, 0, st>>>(
-            s.fluid_cell, s.n_fluid, nx * ny, nz, s.plane_off);
-    LBM_CUDA_TRY(cudaGetLastError());
+    for (size_t b = 0; b < s.parts.size(); ++b) {
+        const Part &P = s.parts[b];
+        if (P.n_links == 0) continue;
+        Bins bins;
+        try {
+            build_bins(P.box, geoms[b]->spheres, bins);
+        } catch (const std::bad_alloc &) {
+            return LBM_ENOMEM;
+        }
+        LBM_CUDA_TRY(cudaMemcpyAsync(d_bstart, bins.start.data(), bins.start.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+        if (!bins.images.empty())
+            LBM_CUDA_TRY(cudaMemcpyAsync(d_img, bins.images.data(), bins.images.size() * sizeof(SphereImage),
+                                         cudaMemcpyHostToDevice, st));
+        const int32_t begin = P.fluid_off, end = P.fluid_off + P.n_fluid;
+        LinkArgs la{s.fluid_cell, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, begin, end,
+                    s.n_fluid, P.cell_base, P.box.nx, P.box.ny, P.box.nz, P.box.periodic_z, bins.nbx, bins.nby,
+                    P.box.q_lo, P.box.q_hi};
+        k_links<<<blocks_for(end - (begin & ~31)), kBlock, 0, st>>>(la);
+        LBM_CUDA_TRY(cudaGetLastError());
+        // the host bins must outlive their (pageable, staged) copies: synchronise
+        LBM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
 
-    uint32_t totals[2] = {0, 0};
-    LBM_CUDA_TRY(cudaMemcpyAsync(totals, d_total, sizeof(totals), cudaMemcpyDeviceToHost, st));
+    LBM_CUDA_TRY(cudaMemcpyAsync(counts.data(), d_total, sizeof(uint32_t) * counts.size(), cudaMemcpyDeviceToHost, st));
     LBM_CUDA_TRY(cudaStreamSynchronize(st));
-    if ((int64_t)totals[0] != s.n_fluid || (int64_t)totals[1] != s.n_links) {
-        std::fprintf(stderr, "liblbm: device list build disagrees with host counts (%u/%lld fluid, %u/%lld links)\n",
-                     totals[0], (long long)s.n_fluid, totals[1], (long long)s.n_links);
+    for (size_t b = 0; b < s.parts.size(); ++b)
+        if ((int64_t)counts[b] != s.parts[b].n_fluid) {
+            std::fprintf(stderr, "liblbm: device list build disagrees with host count of part %zu (%u/%d fluid)\n", b,
+                         counts[b], s.parts[b].n_fluid);
+            return LBM_ECUDA;
+        }
+    if ((int64_t)counts[s.parts.size()] != s.n_links) {
+        std::fprintf(stderr, "liblbm: device link count %u differs from host count %lld\n", counts[s.parts.size()],
+                     (long long)s.n_links);
         return LBM_ECUDA;
     }
     return LBM_OK;

@@ -82,22 +82,50 @@ struct Bins {
     std::vector<SphereImage> images;
 };
 
+// One independent box of a solver.  A solver advances the union of its parts
+// in one launch per step: fluid cells of part b occupy the fluid indices
+// [fluid_off, fluid_off + n_fluid) and the concatenated cell indices
+// [cell_base, cell_base + n_cells); neighbour indices are global, so the step
+// kernels never need to know which part a cell belongs to.
+struct Part {
+    lbm_box box{};
+    int64_t cell_base = 0;
+    int64_t n_cells = 0;
+    int32_t fluid_off = 0;
+    int32_t n_fluid = 0;
+    int64_t n_links = 0;
+    int64_t n_spheres = 0;
+    int32_t plane_base = 0;   // first plane of this part in the concatenated plane arrays
+    int32_t poff_base = 0;    // first entry of this part in plane_off (nz + 1 per part)
+    bool has_prev_profile = false;
+};
+
 // Workspace carve-up.
 struct Layout {
     size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr;
     size_t u_cur, u_prev, rho_cur, prof_prev, bins_start, bins_img, scan_tmp, partials, result, total;
+    size_t part_shift, part_foff;
     // build-time aliases inside the pdf region
     size_t idx_map, mask;
     int32_t n_pad;
     int64_t n_scan_blocks, n_partials;
+    int32_t n_planes;           // sum of nz over parts
+    int32_t n_parts;
 };
 
+// Offsets (in doubles) inside the result region.
+inline size_t res_field(const Layout &L) { return 3 * (size_t)L.n_planes; }        // 3 field-residual sums
+inline size_t res_mass(const Layout &L) { return res_field(L) + 4; }               // 2 global mass sums
+inline size_t res_part(const Layout &L, int b) { return res_mass(L) + 4 + 8 * (size_t)b; }
+// per part: [0] K, [1..3] profile residual sums, [4..5] mass sums
+
 struct Solver {
-    lbm_box box{};
+    lbm_box box{};                 // box of part 0 (the whole solver when unbatched)
     lbm_params params{};
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
     Layout lay{};
+    std::vector<Part> parts;
     int64_t n_cells = 0;
     int32_t n_fluid = 0;
     int32_t n_pad = 0;
@@ -105,13 +133,26 @@ struct Solver {
     int64_t n_spheres = 0;
     int64_t steps = 0;
     bool has_prev = false;
-    bool has_prev_profile = false;
     double omega_p = 0, omega_m = 0, nu = 0;
-    double drho_shift = 0;   // uniform density shift applied by the next step
-    int nbins_x = 0, nbins_y = 0, nbins_z = 0;
-    int n_words = 0;          // 32-cell words per row
-    int x_bits = 0;           // bits of x in cell_xr
-    bool odd_rows = true;     // odd step computes neighbours from row bitmasks
+    bool shift_pending = false;    // the next step applies part_shift
+    std::vector<float> shift_host; // per-part shifts (host copy)
+    int n_words = 0;               // 32-cell words per row (single part)
+    int x_bits = 0;                // bits of x in cell_xr
+    bool odd_rows = true;          // odd step computes neighbours from row bitmasks
+    // launch schedule: grid sizes of the even/odd step (0 = one block per tile)
+    int grid_even = 0, grid_odd = 0;
+    int tune_state = 0;            // 0 untuned, 1 tuning, 2 done
+    int tune_idx = 0;
+    std::vector<int> tune_grids;
+    std::vector<float> tune_ms_even, tune_ms_odd;
+    int tune_count_even = 0, tune_count_odd = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // CUDA graph of kGraphSteps steps starting at even parity
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool use_graph = true;
+    bool autotune = true;
     // device pointers
     void *pdf = nullptr;
     int32_t *nbr = nullptr;
@@ -129,6 +170,9 @@ struct Solver {
     double *prof_prev = nullptr;
     double *partials = nullptr;
     double *result = nullptr;
+    float *part_shift = nullptr;
+    int32_t *part_foff = nullptr;
+    ~Solver();
 };
 
 // ---- host geometry (lbm_geometry.cpp) ----
@@ -138,14 +182,13 @@ void count_fluid_and_links(Geometry &g);
 void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bins);
 
 // ---- workspace (lbm_api.cpp) ----
-Layout make_layout(const lbm_box &box, int64_t n_fluid, int64_t n_links, int storage,
-                   size_t n_bins, size_t n_images);
+Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size_t n_bins, size_t n_images);
 // bits needed for x in cell_xr; rows must fit in the remaining bits
 int x_bits_for(int nx);
 bool rows_packable(const lbm_box &box);
 
 // ---- device build (lbm_build.cu) ----
-int device_build(Solver &s, const Geometry &g, const Bins &bins);
+int device_build(Solver &s, const std::vector<const Geometry *> &geoms);
 
 // ---- step kernels (lbm_step.cu) ----
 int launch_init(Solver &s, const float *dev_u0);
@@ -154,11 +197,11 @@ int launch_steps(Solver &s, int64_t n);
 // ---- post-processing (lbm_post.cu) ----
 int launch_fluid_moments(Solver &s);                       // -> u_cur, rho_cur
 int launch_scatter_moments(Solver &s, float *rho, float *u);
-int launch_plane_average(Solver &s);                       // -> result[0 .. 3 nz)
-int launch_permeability(Solver &s, int z_lo, int z_hi);    // -> result[0]
-int launch_residual(Solver &s);                            // -> result[0..2]
-int launch_mass(Solver &s);                                // -> result[3nz+4]
-int launch_profile_residual(Solver &s);                    // -> result[3nz+1 .. 3nz+3]
+int launch_plane_average(Solver &s);                       // -> result[0 .. 3 n_planes)
+int launch_permeability(Solver &s, int part, int z_lo, int z_hi);  // -> part slot [0]
+int launch_residual(Solver &s);                            // -> res_field
+int launch_profile_residual(Solver &s);                    // -> part slots [1..3]
+int launch_mass(Solver &s);                                // -> res_mass, part slots [4..5]
 int launch_populations(Solver &s, float *out);
 
 // ---- shared host helpers ----

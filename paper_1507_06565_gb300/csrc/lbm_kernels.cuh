@@ -50,7 +50,6 @@ struct Coef {
     float omega_p, omega_m;
     float force[kQ];   // F_k = 3 w_k e_k.g
     float half_g[3];   // g/2, added to j for the reported velocity
-    float shift;       // uniform density shift removed before the collision (0: none)
 };
 
 // Uniform density shift of the logical populations: h_k -= w_k c.

@@ -282,17 +282,21 @@ int launch_plane_average(Solver &s)
 {
     int rc = launch_fluid_moments(s);
     if (rc != LBM_OK) return rc;
-    k_plane_average<<<(unsigned)s.box.nz, kRedThreads, 0, s.stream>>>(s.u_cur, s.plane_off,
-                                                                      (double)s.box.nx * (double)s.box.ny, s.result);
+    for (const Part &P : s.parts)
+        k_plane_average<<<(unsigned)P.box.nz, kRedThreads, 0, s.stream>>>(
+            s.u_cur, s.plane_off + P.poff_base, (double)P.box.nx * (double)P.box.ny, s.result + 3 * (size_t)P.plane_base);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
-int launch_permeability(Solver &s, int z_lo, int z_hi)
+int launch_permeability(Solver &s, int part, int z_lo, int z_hi)
 {
-    int rc = launch_plane_average(s);
-    if (rc != LBM_OK) return rc;
-    k_permeability<<<1, kRedThreads, 0, s.stream>>>(s.result, z_lo, z_hi, s.nu, s.params.g[0],
-                                                    s.result + 3 * (size_t)s.box.nz);
+    if (part == 0 || s.parts.size() == 1) {
+        const int rc = launch_plane_average(s);
+        if (rc != LBM_OK) return rc;
+    }
+    const Part &P = s.parts[part];
+    k_permeability<<<1, kRedThreads, 0, s.stream>>>(s.result + 3 * (size_t)P.plane_base, z_lo, z_hi, s.nu,
+                                                    s.params.g[0], s.result + res_part(s.lay, part));
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
@@ -303,7 +307,7 @@ int launch_residual(Solver &s)
     const int np = (int)s.lay.n_partials;
     k_residual_partials<<<np, kRedThreads, 0, s.stream>>>(s.u_cur, s.u_prev, s.n_fluid, s.n_pad, s.has_prev ? 1 : 0,
                                                           s.partials);
-    k_reduce_partials<<<1, kRedThreads, 0, s.stream>>>(s.partials, np, s.result);
+    k_reduce_partials<<<1, kRedThreads, 0, s.stream>>>(s.partials, np, s.result + res_field(s.lay));
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
@@ -311,8 +315,12 @@ int launch_profile_residual(Solver &s)
 {
     int rc = launch_plane_average(s);
     if (rc != LBM_OK) return rc;
-    k_profile_residual<<<1, kRedThreads, 0, s.stream>>>(s.result, s.prof_prev, s.box.nz, s.has_prev_profile ? 1 : 0,
-                                                        s.result + 3 * (size_t)s.box.nz + 1);
+    for (size_t b = 0; b < s.parts.size(); ++b) {
+        const Part &P = s.parts[b];
+        k_profile_residual<<<1, kRedThreads, 0, s.stream>>>(s.result + 3 * (size_t)P.plane_base,
+                                                            s.prof_prev + P.plane_base, P.box.nz,
+                                                            P.has_prev_profile ? 1 : 0, s.result + res_part(s.lay, (int)b) + 1);
+    }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
@@ -322,7 +330,12 @@ int launch_mass(Solver &s)
     if (rc != LBM_OK) return rc;
     const int np = (int)s.lay.n_partials;
     k_mass_partials<<<np, kRedThreads, 0, s.stream>>>(s.rho_cur, s.n_fluid, s.partials);
-    k_reduce_partials<<<1, kRedThreads, 0, s.stream>>>(s.partials, np, s.result + 3 * (size_t)s.box.nz + 4);
+    k_reduce_partials<<<1, kRedThreads, 0, s.stream>>>(s.partials, np, s.result + res_mass(s.lay));
+    for (size_t b = 0; b < s.parts.size(); ++b) {
+        const Part &P = s.parts[b];
+        k_mass_partials<<<np, kRedThreads, 0, s.stream>>>(s.rho_cur + P.fluid_off, P.n_fluid, s.partials);
+        k_reduce_partials<<<1, kRedThreads, 0, s.stream>>>(s.partials, np, s.result + res_part(s.lay, (int)b) + 4);
+    }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 

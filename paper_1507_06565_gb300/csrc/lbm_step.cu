@@ -1,10 +1,18 @@
 // lbm_step.cu -- the fused stream-collide + CLI update over the sparse fluid
-// list (in-place AA pattern, see lbm_kernels.cuh) and the initialisation.
+// list (in-place AA pattern, see lbm_kernels.cuh), the initialisation, and the
+// launch schedule (tile-loop grid chosen by timing, CUDA-graph replay).
 //
-// One thread per fluid cell, 256 threads per block.  The even step touches only
-// the cell's own 19 slots (contiguous structure-of-arrays rows, fully
-// coalesced); the odd step gathers through the neighbour table and scatters
-// back to the same slots.  Wall links cost one coefficient load each.
+// One thread per fluid cell; a block handles tiles of 256 consecutive fluid
+// cells (8 aligned warps) and loops over tiles with the grid stride, so a grid
+// smaller than the tile count makes the kernel persistent.  The even step
+// touches only the cell's own 19 slots (contiguous structure-of-arrays rows);
+// the odd step gathers through the neighbour indices and scatters back to the
+// same slots.  Wall links cost one coefficient load each.  The kernels never
+// need to know which independent box (part) a cell belongs to, because the
+// neighbour indices are global; only the optional density re-centring looks
+// up the part of a cell.
+#include <algorithm>
+
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -16,6 +24,8 @@ namespace {
 // odd step is best at 4 (64 registers); more blocks make the odd step spill.
 constexpr int kEvenBlocksPerSM = 5;
 constexpr int kOddBlocksPerSM = 4;
+constexpr int kGraphSteps = 32;     // steps per CUDA-graph replay (even)
+constexpr int kTuneReps = 3;        // timed launches per candidate grid
 
 template <typename T>
 struct StepArgs {
@@ -26,21 +36,37 @@ struct StepArgs {
     const float *link_a;
     int32_t n_fluid;
     int32_t n_pad;
+    int32_t n_tiles;
     RowGeo rows;
+    const float *part_shift;   // per-part density shift
+    const int32_t *part_foff;  // [n_parts + 1] first fluid index of each part
+    int32_t n_parts;
+    int32_t shift_on;          // apply part_shift in this launch
     Coef c;
 };
+
+// Density shift of the part that holds fluid cell i (binary search).
+template <typename T>
+__device__ __forceinline__ float part_shift_of(const StepArgs<T> &p, int32_t i)
+{
+    int lo = 0, hi = p.n_parts - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(p.part_foff + mid) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return __ldg(p.part_shift + lo);
+}
 
 // Per-thread staging in shared memory: the CLI coefficients (and, for the odd
 // step, the neighbour indices) of a thread are written and read by that thread
 // only, so no barrier is needed.  Keeping them out of registers across the
 // collision lowers register pressure and raises the number of resident warps,
 // which is what hides the memory latency of these kernels.
-template <typename T, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
+template <typename T>
+__device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i, float (*a_s)[kBlock])
 {
-    __shared__ float a_s[kQ - 1][kBlock];
     const int t = threadIdx.x;
-    const int32_t i = blockIdx.x * kBlock + t;
     const bool live = i < p.n_fluid;
     const uint32_t m = live ? p.lmask[i] : 0u;
     const uint32_t off = first_link(p.warp_off, i, m);
@@ -52,7 +78,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
         stage_links(a_s, t, m, p.link_a, off);
         cli_incoming_s(h, a_s, t);
     }
-    apply_shift(h, p.c.shift);
+    if (p.shift_on) apply_shift(h, part_shift_of(p, i));
     collide(h, p.c);
     if (m) cli_outgoing_s(h, a_s, t);
 #pragma unroll
@@ -60,13 +86,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
 }
 
 // ROWS: neighbour indices from the row bitmasks; otherwise from the table.
-template <typename T, bool ROWS, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
+template <typename T, bool ROWS>
+__device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock],
+                                         float (*a_s)[kBlock])
 {
-    __shared__ int32_t nb_s[kQ - 1][kBlock];
-    __shared__ float a_s[kQ - 1][kBlock];
     const int t = threadIdx.x;
-    const int32_t i = blockIdx.x * kBlock + t;
     const bool live = i < p.n_fluid;
     // 32-bit element offsets (19 n_pad < 2^32 is checked on the host)
     const uint32_t n_pad = (uint32_t)p.n_pad, ui = (uint32_t)i;
@@ -88,7 +112,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
         h[k] = ld(p.pdf + (up >= 0 ? opp(k) * n_pad + (uint32_t)up : k * n_pad + ui));
     }
     if (m) cli_incoming_s(h, a_s, t);
-    apply_shift(h, p.c.shift);
+    if (p.shift_on) apply_shift(h, part_shift_of(p, i));
     collide(h, p.c);
     if (m) cli_outgoing_s(h, a_s, t);
     st(p.pdf + ui, h[0]);
@@ -97,6 +121,22 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
         const int32_t down = nb_s[k - 1][t];
         st(p.pdf + (down >= 0 ? k * n_pad + (uint32_t)down : opp(k) * n_pad + ui), h[k]);
     }
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
+{
+    __shared__ float a_s[kQ - 1][kBlock];
+    for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) even_cell(p, tile * kBlock + threadIdx.x, a_s);
+}
+
+template <typename T, bool ROWS, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
+{
+    __shared__ int32_t nb_s[kQ - 1][kBlock];
+    __shared__ float a_s[kQ - 1][kBlock];
+    for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x)
+        odd_cell<T, ROWS>(p, tile * kBlock + threadIdx.x, nb_s, a_s);
 }
 
 // Initial state f_k = f_k^eq(rho = 1, u0) (Eq. (equilibrium)) stored shifted
@@ -137,7 +177,7 @@ __global__ void __launch_bounds__(kBlock) k_init(StepArgs<T> p, const int32_t *_
 }
 
 template <typename T>
-StepArgs<T> make_args(Solver &s)
+StepArgs<T> make_args(const Solver &s)
 {
     StepArgs<T> p;
     p.pdf = (T *)s.pdf;
@@ -147,7 +187,12 @@ StepArgs<T> make_args(Solver &s)
     p.link_a = s.link_a;
     p.n_fluid = s.n_fluid;
     p.n_pad = s.n_pad;
+    p.n_tiles = s.n_pad / kBlock;
     p.rows = RowGeo{s.row_words, s.cell_xr, s.box.nx, s.box.ny, s.box.nz, s.n_words, s.x_bits, s.box.periodic_z};
+    p.part_shift = s.part_shift;
+    p.part_foff = s.part_foff;
+    p.n_parts = (int32_t)s.parts.size();
+    p.shift_on = 0;
     p.c.omega_p = (float)s.omega_p;
     p.c.omega_m = (float)s.omega_m;
     for (int k = 0; k < kQ; ++k) {
@@ -155,8 +200,43 @@ StepArgs<T> make_args(Solver &s)
         p.c.force[k] = (float)(3.0 * weight(k) * eg);
     }
     for (int d = 0; d < 3; ++d) p.c.half_g[d] = (float)(0.5 * s.params.g[d]);
-    p.c.shift = 0.0f;
     return p;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+// One step launch at the current parity with the chosen grid (0: a block per tile).
+template <typename T>
+void launch_step(const Solver &s, const StepArgs<T> &p, bool odd, int grid, cudaStream_t st)
+{
+    const unsigned g = (unsigned)(grid > 0 ? std::min(grid, p.n_tiles) : p.n_tiles);
+    if (!odd) k_step_even<T, kEvenBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    else if (s.odd_rows) k_step_odd<T, true, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    else k_step_odd<T, false, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+}
+
+// Candidate grids: a block per tile, or 1, 2, 4 waves of resident blocks
+// looping over the tiles.  Only solvers of more than four waves are tuned.
+void start_tuning(Solver &s, int n_tiles)
+{
+    const int wave = sm_count() * kOddBlocksPerSM;
+    s.tune_grids = {0};
+    if (s.autotune && n_tiles > 4 * sm_count() * kEvenBlocksPerSM)
+        for (int w : {1, 2, 4}) s.tune_grids.push_back(w * wave);
+    s.tune_ms_even.assign(s.tune_grids.size(), 0.0f);
+    s.tune_ms_odd.assign(s.tune_grids.size(), 0.0f);
+    s.tune_count_even = s.tune_count_odd = 0;
+    s.tune_state = s.tune_grids.size() > 1 ? 1 : 2;
+    s.grid_even = s.grid_odd = 0;
+    if (s.tune_state == 1 && (!s.ev0 || !s.ev1)) {
+        if (cudaEventCreate(&s.ev0) != cudaSuccess || cudaEventCreate(&s.ev1) != cudaSuccess) s.tune_state = 2;
+    }
 }
 
 template <typename T>
@@ -167,15 +247,60 @@ int run_steps(Solver &s, int64_t n)
         return LBM_OK;
     }
     StepArgs<T> p = make_args<T>(s);
-    const unsigned grid = (unsigned)(s.n_pad / kBlock);
-    for (int64_t t = 0; t < n; ++t) {
-        p.c.shift = t == 0 ? (float)s.drho_shift : 0.0f;
-        if ((s.steps & 1) == 0) k_step_even<T, kEvenBlocksPerSM><<<grid, kBlock, 0, s.stream>>>(p);
-        else if (s.odd_rows) k_step_odd<T, true, kOddBlocksPerSM><<<grid, kBlock, 0, s.stream>>>(p);
-        else k_step_odd<T, false, kOddBlocksPerSM><<<grid, kBlock, 0, s.stream>>>(p);
+    if (s.tune_state == 0) start_tuning(s, p.n_tiles);
+    const int C = (int)s.tune_grids.size();
+    int64_t t = 0;
+    while (t < n) {
+        const bool odd = (s.steps & 1) != 0;
+        p.shift_on = s.shift_pending ? 1 : 0;
+        s.shift_pending = false;
+        if (s.tune_state == 1) {
+            int &cnt = odd ? s.tune_count_odd : s.tune_count_even;
+            if (cnt < C * kTuneReps) {
+                const int c = cnt / kTuneReps;
+                if (cudaEventRecord(s.ev0, s.stream) != cudaSuccess) return LBM_ECUDA;
+                launch_step(s, p, odd, s.tune_grids[c], s.stream);
+                if (cudaEventRecord(s.ev1, s.stream) != cudaSuccess || cudaEventSynchronize(s.ev1) != cudaSuccess)
+                    return LBM_ECUDA;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, s.ev0, s.ev1);
+                (odd ? s.tune_ms_odd : s.tune_ms_even)[c] += ms;
+                ++cnt;
+            } else {
+                launch_step(s, p, odd, odd ? s.grid_odd : s.grid_even, s.stream);
+            }
+            if (s.tune_count_even >= C * kTuneReps && s.tune_count_odd >= C * kTuneReps) {
+                s.grid_even = s.tune_grids[std::min_element(s.tune_ms_even.begin(), s.tune_ms_even.end()) -
+                                           s.tune_ms_even.begin()];
+                s.grid_odd = s.tune_grids[std::min_element(s.tune_ms_odd.begin(), s.tune_ms_odd.end()) -
+                                          s.tune_ms_odd.begin()];
+                s.tune_state = 2;
+            }
+            ++s.steps;
+            ++t;
+            continue;
+        }
+        // replay whole graph chunks from an even step, once the schedule is fixed
+        if (s.use_graph && !odd && !p.shift_on && n - t >= kGraphSteps) {
+            if (!s.graph_exec) {
+                if (!s.cap_stream && cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    return LBM_ECUDA;
+                if (cudaStreamBeginCapture(s.cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return LBM_ECUDA;
+                for (int k = 0; k < kGraphSteps; ++k) launch_step(s, p, (k & 1) != 0, (k & 1) ? s.grid_odd : s.grid_even, s.cap_stream);
+                if (cudaStreamEndCapture(s.cap_stream, &s.graph) != cudaSuccess) return LBM_ECUDA;
+                if (cudaGraphInstantiate(&s.graph_exec, s.graph, 0) != cudaSuccess) return LBM_ECUDA;
+            }
+            while (n - t >= kGraphSteps) {
+                if (cudaGraphLaunch(s.graph_exec, s.stream) != cudaSuccess) return LBM_ECUDA;
+                s.steps += kGraphSteps;
+                t += kGraphSteps;
+            }
+            continue;
+        }
+        launch_step(s, p, odd, odd ? s.grid_odd : s.grid_even, s.stream);
         ++s.steps;
+        ++t;
     }
-    if (n > 0) s.drho_shift = 0.0;
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
@@ -183,7 +308,7 @@ template <typename T>
 int run_init(Solver &s, const float *u0)
 {
     s.steps = 0;
-    s.drho_shift = 0.0;
+    s.shift_pending = false;
     if (s.n_fluid == 0) return LBM_OK;
     const StepArgs<T> p = make_args<T>(s);
     k_init<T><<<(unsigned)(s.n_pad / kBlock), kBlock, 0, s.stream>>>(p, s.fluid_cell, u0, s.n_cells);
@@ -192,10 +317,16 @@ int run_init(Solver &s, const float *u0)
 
 }  // namespace
 
-Coef make_coef(const Solver &s)
+Solver::~Solver()
 {
-    return make_args<float>(const_cast<Solver &>(s)).c;
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
 }
+
+Coef make_coef(const Solver &s) { return make_args<float>(s).c; }
 
 int launch_init(Solver &s, const float *dev_u0)
 {
@@ -217,4 +348,18 @@ int launch_steps(Solver &s, int64_t n)
     return LBM_EINVAL;
 }
 
+int graph_steps() { return kGraphSteps; }
+
 }  // namespace lbm
+
+extern "C" int lbm_schedule(const lbm_solver *s, int32_t *grid_even, int32_t *grid_odd, int32_t *tuned,
+                            int32_t *graph_steps_out)
+{
+    if (!s) return LBM_EINVAL;
+    const int32_t tiles = s->n_pad / lbm::kBlock;
+    if (grid_even) *grid_even = s->grid_even > 0 ? std::min(s->grid_even, tiles) : tiles;
+    if (grid_odd) *grid_odd = s->grid_odd > 0 ? std::min(s->grid_odd, tiles) : tiles;
+    if (tuned) *tuned = s->tune_state == 2 ? 1 : 0;
+    if (graph_steps_out) *graph_steps_out = s->use_graph ? lbm::graph_steps() : 0;
+    return LBM_OK;
+}
