@@ -30,8 +30,10 @@
  * F_k = 3 w_k e_k.g added after relaxation with the equilibrium built from the
  * pre-collision momentum j, and the reported velocity u = j + g/2; full
  * (unshifted) populations with rho = sum f; the second fluid node of a link is
- * x_f1 - e_k and when it is solid the link falls back to bounce-back; q is the
- * first point of the link on a solid surface (smallest entry parameter);
+ * x_f2 = x_f1 - e_k, and the link falls back to bounce-back when x_f2 is solid
+ * or q < 0.1 (a stability safeguard for sharp corners, see orc_link_fallback);
+ * q is the first point of the link on a solid surface (smallest entry
+ * parameter);
  * seeded sphere placement (SplitMix64) stands in for the rigid-body packing.
  *
  * Plain loops, no blocking or fusion beyond the definition; OpenMP only splits
@@ -426,6 +428,20 @@ static int64_t orc_neighbour(const orc_box *b, int x, int y, int z, int k)
     return orc_cell(b, xn, yn, zn);
 }
 
+/* Bounce-back fallback of link (x, k) with fraction q: Eq. (CLI) needs the
+ * second fluid node x_f2 = x_f1 - e_k, so the link uses simple bounce-back
+ * (a = 0) when x_f2 is solid.  It also does when q < ORC_CLI_QMIN: for a wall
+ * within a tenth of a link of the node the interpolation weight
+ * a = (1-2q)/(1+2q) exceeds 2/3 and, in the sharp corners between
+ * overlapping spheres (nodes with most of their 18 neighbours solid), the
+ * update was observed to grow without bound; bounce-back there is stable. */
+#define ORC_CLI_QMIN 0.1
+static int orc_link_fallback(const orc_box *b, const uint8_t *solid, int x, int y, int z, int k, double q)
+{
+    int64_t c2 = orc_neighbour(b, x, y, z, orc_opp(k));
+    return c2 < 0 || solid[c2] || q < ORC_CLI_QMIN;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Fluid list, neighbour table and wall-link list.                            */
 /* fluid_cell[i]  : linear cell index (x fastest) of the i-th fluid cell, in  */
@@ -433,7 +449,7 @@ static int64_t orc_neighbour(const orc_box *b, int x, int y, int z, int k)
 /* nbr[(k-1)*nf+i]: fluid index of the neighbour along e_k, -1 when solid.    */
 /* links          : one record per (fluid cell, k) with a solid neighbour,   */
 /*                  sorted by (cell, k): cell index i, k, q, and whether the  */
-/*                  second fluid node x_f1 - e_k is solid (bounce-back then). */
+/*                  link falls back to bounce-back (orc_link_fallback).       */
 /* Call with fluid_cell == NULL to get counts only.                           */
 /* ------------------------------------------------------------------------- */
 int orc_build_lists(int nx, int ny, int nz, int periodic_z, double q_lo, double q_hi,
@@ -466,12 +482,11 @@ int orc_build_lists(int nx, int ny, int nz, int periodic_z, double q_lo, double 
                     if (nbr) nbr[(int64_t)(k - 1) * nf + i] = in;
                     if (in >= 0) continue;
                     if (link_cell) {
-                        int64_t c2 = orc_neighbour(&b, x, y, z, orc_opp(k));
                         link_cell[nl] = i;
                         link_k[nl] = (int8_t)k;
                         link_q[nl] = use_bins ? orc_link_q_binned(&b, xyzr, &bins, x, y, z, k)
                                               : orc_link_q_impl(&b, xyzr, n, x, y, z, k);
-                        link_fallback[nl] = (uint8_t)(c2 < 0 || solid[c2]);
+                        link_fallback[nl] = (uint8_t)orc_link_fallback(&b, solid, x, y, z, k, link_q[nl]);
                     }
                     ++nl;
                 }
@@ -569,10 +584,10 @@ orc_lbm *orc_lbm_create(int nx, int ny, int nz, int periodic_z, double q_lo, dou
                 for (int k = 1; k < NQ; ++k) {
                     int64_t cn = orc_neighbour(&s->b, x, y, z, k);
                     if (cn >= 0 && !s->solid[cn]) continue;
-                    int64_t c2 = orc_neighbour(&s->b, x, y, z, orc_opp(k));
                     double q = orc_link_q_binned(&s->b, xyzr, &bins, x, y, z, k);
                     s->link_k[l] = (int8_t)k;
-                    s->link_a[l] = (c2 < 0 || s->solid[c2]) ? 0.0 : (1.0 - 2.0 * q) / (1.0 + 2.0 * q);
+                    s->link_a[l] = orc_link_fallback(&s->b, s->solid, x, y, z, k, q) ? 0.0
+                                                                                  : (1.0 - 2.0 * q) / (1.0 + 2.0 * q);
                     ++l;
                 }
             }
@@ -655,7 +670,8 @@ static void orc_collide(orc_lbm *s)
  * (Eq. (CLI)): for a fluid node x_f1 whose neighbour x_b = x_f1 + e_k is solid,
  *   f_kbar(x_f1, t+1) = a f~_k(x_f2) - a f~_kbar(x_f1) + f~_k(x_f1),
  *   a = (1-2q)/(1+2q),  x_f2 = x_f1 - e_k,
- * and a = 0 (simple bounce-back, Eq. (noslip)) when x_f2 is solid. */
+ * and a = 0 (simple bounce-back, Eq. (noslip)) on the fallback links of
+ * orc_link_fallback. */
 static void orc_stream(orc_lbm *s)
 {
     const int64_t N = s->ncell;
