@@ -30,8 +30,9 @@
  * F_k = 3 w_k e_k.g added after relaxation with the equilibrium built from the
  * pre-collision momentum j, and the reported velocity u = j + g/2; full
  * (unshifted) populations with rho = sum f; the second fluid node of a link is
- * x_f2 = x_f1 - e_k, and the link falls back to bounce-back when x_f2 is solid
- * or q < 0.1 (a stability safeguard for sharp corners, see orc_link_fallback);
+ * x_f2 = x_f1 - e_k, and the link falls back to bounce-back when x_f2 is solid,
+ * when x_f1 - 2 e_k is solid, or when q < 0.1 (stability safeguards for sharp
+ * corners, see orc_link_fallback);
  * q is the first point of the link on a solid surface (smallest entry
  * parameter);
  * seeded sphere placement (SplitMix64) stands in for the rigid-body packing.
@@ -428,18 +429,27 @@ static int64_t orc_neighbour(const orc_box *b, int x, int y, int z, int k)
     return orc_cell(b, xn, yn, zn);
 }
 
-/* Bounce-back fallback of link (x, k) with fraction q: Eq. (CLI) needs the
+/* Bounce-back fallback of link (x, k) with fraction q.  Eq. (CLI) needs the
  * second fluid node x_f2 = x_f1 - e_k, so the link uses simple bounce-back
- * (a = 0) when x_f2 is solid.  It also does when q < ORC_CLI_QMIN: for a wall
- * within a tenth of a link of the node the interpolation weight
- * a = (1-2q)/(1+2q) exceeds 2/3 and, in the sharp corners between
- * overlapping spheres (nodes with most of their 18 neighbours solid), the
- * update was observed to grow without bound; bounce-back there is stable. */
+ * (a = 0) when x_f2 is solid.  Two more cases take bounce-back because the
+ * FP64 update was observed to grow without bound there, in the sharp corners
+ * of overlapping sphere packings (nodes with most of their 18 links cut):
+ *   - x_f2 is itself a wall node on the link's line (x_f1 - 2 e_k solid: a
+ *     two-cell gap, where the two interpolations feed each other);
+ *   - q < ORC_CLI_QMIN: the wall within a tenth of a link of the node, where
+ *     a = (1-2q)/(1+2q) > 2/3 weights the non-local term almost fully.
+ * Either case alone left some corners unstable; together they stabilised
+ * every one found. */
 #define ORC_CLI_QMIN 0.1
 static int orc_link_fallback(const orc_box *b, const uint8_t *solid, int x, int y, int z, int k, double q)
 {
-    int64_t c2 = orc_neighbour(b, x, y, z, orc_opp(k));
-    return c2 < 0 || solid[c2] || q < ORC_CLI_QMIN;
+    const int kb = orc_opp(k);
+    int64_t c2 = orc_neighbour(b, x, y, z, kb);
+    if (c2 < 0 || solid[c2] || q < ORC_CLI_QMIN) return 1;
+    int x2 = orc_wrap(x + ORC_EX[kb], b->nx), y2 = orc_wrap(y + ORC_EY[kb], b->ny), z2 = z + ORC_EZ[kb];
+    if (b->periodic_z) z2 = orc_wrap(z2, b->nz);
+    int64_t c3 = orc_neighbour(b, x2, y2, z2, kb);
+    return c3 < 0 || solid[c3];
 }
 
 /* ------------------------------------------------------------------------- */
