@@ -6,7 +6,9 @@
  * two-relaxation-time scheme (Sec. 2.1, Eqs. (LBM), (TRT), (TRT2),
  * (equilibrium), (Macro), (collision), (streaming)) driven by a body force,
  * with central-linear-interpolation bounce-back on every wall link
- * (Sec. 2.2, Eq. (CLI); q = 1/2 is simple bounce-back, Eq. (noslip)), on
+ * (Sec. 2.2, Eq. (CLI); q = 1/2 is simple bounce-back, Eq. (noslip); links
+ * without a second fluid node, across a two-cell gap or with q < 0.1 use
+ * bounce-back), on
  * voxelised sphere packings (Sec. 3.1), with plane averages of the stream-wise
  * velocity (Sec. 3.1) and the Darcy permeability (Eq. (Darcy)).
  *
@@ -289,8 +291,12 @@ int lbm_solver_info(const lbm_solver *solver, lbm_geometry_info *out);
  * fluid_cell[n_fluid] cell index of each fluid cell; nbr[18][n_fluid] fluid
  * index of the neighbour along e_k (k = 1..18) or -1 when solid;
  * link_cell/link_k/link_q/link_fallback[n_links]: one record per wall link in
- * (cell, k) order with the link fraction q of Eq. (CLI) and 1 when the second
- * fluid node x_f1 - e_k is solid (the link then uses bounce-back, a = 0).
+ * (cell, k) order with the link fraction q of Eq. (CLI) and 1 when the link
+ * uses simple bounce-back (a = 0) instead: when its second fluid node
+ * x_f2 = x_f1 - e_k is solid, when x_f1 - 2 e_k is solid (a two-cell gap),
+ * or when q < 0.1 (the wall within a tenth of a link of the node).  In the
+ * sharp corners of overlapping sphere packings Eq. (CLI) on the last two
+ * kinds of link was observed to grow without bound.
  * Synchronises the stream. */
 int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int32_t *link_cell,
                      int8_t *link_k, double *link_q, uint8_t *link_fallback);

@@ -613,26 +613,38 @@ int lbm_export_lists(lbm_solver *s, int32_t *fluid_cell, int32_t *nbr, int32_t *
         cudaMemcpyAsync(link_q, s->link_q, (size_t)s->n_links * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return LBM_ECUDA;
     if (link_cell || link_k || link_fallback) {
-        uint32_t *mask = new (std::nothrow) uint32_t[nf ? nf : 1];
-        if (!mask) return LBM_ENOMEM;
-        if (nf && cudaMemcpyAsync(mask, s->lmask, nf * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-            delete[] mask;
-            return LBM_ECUDA;
+        // links in (cell, k) order from the link masks; a link falls back to
+        // bounce-back when x - e_k or x - 2 e_k is solid or q < kCliQmin
+        std::vector<uint32_t> mask(nf ? nf : 1);
+        std::vector<double> qs;
+        std::vector<int32_t> nb;
+        if (link_fallback) {
+            qs.resize(s->n_links ? (size_t)s->n_links : 1);
+            nb.resize((size_t)(kQ - 1) * (nf ? nf : 1));
         }
-        if (cudaStreamSynchronize(st) != cudaSuccess) {
-            delete[] mask;
+        if (nf && cudaMemcpyAsync(mask.data(), s->lmask, nf * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return LBM_ECUDA;
-        }
+        if (link_fallback && s->n_links &&
+            cudaMemcpyAsync(qs.data(), s->link_q, (size_t)s->n_links * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return LBM_ECUDA;
+        if (link_fallback && nf &&
+            cudaMemcpy2DAsync(nb.data(), nf * 4, s->nbr, (size_t)s->n_pad * 4, nf * 4, kQ - 1, cudaMemcpyDeviceToHost,
+                              st) != cudaSuccess)
+            return LBM_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return LBM_ECUDA;
         size_t l = 0;
         for (size_t i = 0; i < nf; ++i)
             for (int k = 1; k < kQ; ++k)
                 if ((mask[i] >> k) & 1u) {
                     if (link_cell) link_cell[l] = (int32_t)i;
                     if (link_k) link_k[l] = (int8_t)k;
-                    if (link_fallback) link_fallback[l] = (uint8_t)((mask[i] >> opp(k)) & 1u);
+                    if (link_fallback) {
+                        bool fb = ((mask[i] >> opp(k)) & 1u) || qs[l] < kCliQmin;
+                        if (!fb) fb = (mask[nb[(size_t)(opp(k) - 1) * nf + i]] >> opp(k)) & 1u;
+                        link_fallback[l] = (uint8_t)fb;
+                    }
                     ++l;
                 }
-        delete[] mask;
     }
     return cudaStreamSynchronize(st) == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }

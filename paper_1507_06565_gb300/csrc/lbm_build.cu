@@ -12,7 +12,8 @@
 // then over the whole solver: link counts per aligned group of 32 fluid cells
 // and their exclusive scan; and again per part:
 //   5. link fraction q and CLI coefficient a = (1-2q)/(1+2q) per link
-//      (a = 0, bounce-back, when the second node x - e_k is solid).
+//      (a = 0, bounce-back, when the second node x - e_k is solid, when
+//      x - 2 e_k is solid, or when q < 0.1).
 // The index map and the mask live in the population region, which is written
 // only afterwards by the initialisation.
 #include <cstdio>
@@ -184,13 +185,14 @@ __device__ double sphere_entry(double dx, double dy, double dz, int kx, int ky, 
 
 struct LinkArgs {
     const int32_t *fluid_cell;
+    const int32_t *nbr;
     const uint32_t *lmask;
     const uint32_t *warp_off;
     const int32_t *bin_start;
     const SphereImage *images;
     float *link_a;
     double *link_q;
-    int32_t begin, end, n_fluid;
+    int32_t begin, end, n_fluid, n_pad;
     int64_t cell_base;
     int nx, ny, nz, periodic_z;
     int nbx, nby;
@@ -237,7 +239,15 @@ __global__ void k_links(LinkArgs a)
             const double s = sphere_entry((double)x - im.x, (double)y - im.y, (double)z - im.z, kx, ky, kz, im.r);
             if (s < q) q = s;
         }
-        const bool fallback = (m >> opp(k)) & 1u;
+        // bounce-back when the second node x_f2 = x - e_k is solid, is itself a
+        // wall node on the link's line (x - 2 e_k solid), or when the wall is
+        // within kCliQmin of the node: Eq. (CLI) grows without bound in such
+        // sharp corners of overlapping packings
+        bool fallback = ((m >> opp(k)) & 1u) || q < kCliQmin;
+        if (!fallback) {
+            const int32_t x2 = a.nbr[(size_t)(opp(k) - 1) * a.n_pad + i];
+            fallback = (a.lmask[x2] >> opp(k)) & 1u;
+        }
         const double coef = fallback ? 0.0 : __ddiv_rn(__dsub_rn(1.0, __dmul_rn(2.0, q)), __dadd_rn(1.0, __dmul_rn(2.0, q)));
         a.link_q[off] = q;
         a.link_a[off] = (float)coef;
@@ -334,9 +344,9 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
             LBM_CUDA_TRY(cudaMemcpyAsync(d_img, bins.images.data(), bins.images.size() * sizeof(SphereImage),
                                          cudaMemcpyHostToDevice, st));
         const int32_t begin = P.fluid_off, end = P.fluid_off + P.n_fluid;
-        LinkArgs la{s.fluid_cell, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, begin, end,
-                    s.n_fluid, P.cell_base, P.box.nx, P.box.ny, P.box.nz, P.box.periodic_z, bins.nbx, bins.nby,
-                    P.box.q_lo, P.box.q_hi};
+        LinkArgs la{s.fluid_cell, s.nbr, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, begin, end,
+                    s.n_fluid, s.n_pad, P.cell_base, P.box.nx, P.box.ny, P.box.nz, P.box.periodic_z, bins.nbx,
+                    bins.nby, P.box.q_lo, P.box.q_hi};
         k_links<<<blocks_for(end - (begin & ~31)), kBlock, 0, st>>>(la);
         LBM_CUDA_TRY(cudaGetLastError());
         // the host bins must outlive their (pageable, staged) copies: synchronise

@@ -213,9 +213,10 @@ void count_fluid_and_links(Geometry &g)
 }
 
 // Every sphere image is listed in each bin of kBinEdge^3 cells that its
-// bounding box grown by two cells overlaps.  A link starting in a bin is at
-// most sqrt(2) long, so it can only enter images listed for that bin.
-void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bins)
+// bounding box grown by `grow` cells overlaps.  With grow = 2 a link starting
+// in a bin (at most sqrt(2) long) can only enter images listed for that bin;
+// with grow = T every image within distance T of a cell of the bin is listed.
+void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bins, double grow)
 {
     bins.nbx = (box.nx + kBinEdge - 1) / kBinEdge;
     bins.nby = (box.ny + kBinEdge - 1) / kBinEdge;
@@ -235,8 +236,8 @@ void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bi
                     int lo[3], hi[3];
                     bool empty = false;
                     for (int a = 0; a < 3; ++a) {
-                        lo[a] = std::max(0, (int)std::floor(c[a] - im.r - 2.0));
-                        hi[a] = std::min(ext[a] - 1, (int)std::ceil(c[a] + im.r + 2.0));
+                        lo[a] = std::max(0, (int)std::floor(c[a] - im.r - grow));
+                        hi[a] = std::min(ext[a] - 1, (int)std::ceil(c[a] + im.r + grow));
                         empty |= lo[a] > hi[a];
                     }
                     if (empty) continue;

@@ -21,6 +21,7 @@
 // first link of cell i is warp_off[i/32] + (links of cells i&~31 .. i-1).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -34,6 +35,10 @@ namespace lbm {
 constexpr int kQ = 19;
 constexpr int kBlock = 256;   // threads per block of the per-cell kernels
 constexpr int kBinEdge = 8;   // edge (cells) of the sphere-image bins
+// Links whose wall lies closer than this fraction of the link to the node use
+// simple bounce-back instead of Eq. (CLI) (stability in sharp corners, with
+// the two-cell-gap rule of k_links).
+constexpr double kCliQmin = 0.1;
 
 // ---------------------------------------------------------------------------
 // D3Q19 velocity set (ordering documented in lbm.h).
@@ -179,7 +184,7 @@ struct Solver {
 int place_and_voxelise(const lbm_sphere_params &p, Geometry &g);
 int voxelise_list(const lbm_box &box, const double *xyzr, int64_t n, Geometry &g);
 void count_fluid_and_links(Geometry &g);
-void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bins);
+void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bins, double grow = 2.0);
 
 // ---- workspace (lbm_api.cpp) ----
 Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size_t n_bins, size_t n_images);
