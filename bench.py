@@ -144,6 +144,91 @@ def cpu_baseline(seconds_hint: float = 15.0):
             "sample": f"{SAMPLE.name} ({nf} fluid cells), FP64 dense two-array oracle, {n} steps after 1 warm-up"}
 
 
+def workload_name(args):
+    if args.workload == "channel":
+        return WORKLOAD
+    if args.workload == "channel-half":
+        return WORKLOAD.replace("256x256x512", "128x128x256")
+    return (f"{args.cubes} periodic REV cubes (edge U[48,160], r U[3,10], porosity U[0.35,0.95], seeds 4000+i) "
+            "as one batch: one launch per step for all cubes")
+
+
+def run_converge(args):
+    """Time to steady state: run the workload until the plane-profile residual
+    (largest over the parts) is below --tol, re-centring the density at every
+    check; report wall time, steps and the permeability of every box."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    if args.workload == "rev":
+        cases = [W.W4_cube(i) for i in range(args.cubes)]
+        geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
+        solvers = [L.BatchSolver(geoms, cases[0].tau, cases[0].lam, cases[0].g, args.storage)]
+    else:
+        cases = [W.W2(phi) for phi in W.W2_POROSITIES] if args.workload == "channel" else [
+            W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True, W.W2(phi).seed)
+            for phi in W.W2_POROSITIES]
+        geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
+        solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage) for g, c in zip(geoms, cases)]
+    out = []
+    total_s = 0.0
+    for s, c in zip(solvers, cases):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, n, res = s.run_until(args.tol, args.interval, args.max_steps, criterion="profile")
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        total_s += dt
+        if isinstance(s, L.BatchSolver):
+            k = s.permeabilities().tolist()
+        else:
+            k = [s.permeability(*c.perm_window)]
+        out.append({"status": L.status_string(rc), "steps": n, "residual": res, "seconds": dt,
+                    "mlups": s.info()["n_fluid"] * n / dt / 1e6, "permeability": k, "schedule": s.schedule()})
+    line = {"metric": f"time to steady state (plane-profile residual < {args.tol:g})", "value": total_s, "unit": "s",
+            "higher_is_better": False, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": workload_name(args)}, "runs": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_surrogate(args):
+    """Time to steady state with and without the learned warm start: solver-
+    generated training data, training with the library's U-Net kernels, and
+    cold versus warm runs of held-out packings to the same tolerance."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300 import surrogate as S
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    shape = (64, 64, 128)
+    t0 = time.perf_counter()
+    data = S.generate(range(500000, 500000 + args.train_samples), shape, tol=1e-6)
+    tr = S.train(data, epochs=args.epochs, lr=2e-3, batch=4)
+    params = tr.net.params().cpu().numpy()
+    rows = S.warm_vs_cold(params, range(600000, 600000 + args.heldout), shape, tol=args.tol)
+    cold = sum(r["cold"]["seconds"] for r in rows)
+    warm = sum(r["warm"]["seconds"] for r in rows)
+    line = {"metric": f"time to steady state (plane-profile residual < {args.tol:g}), surrogate warm vs cold",
+            "value": warm, "unit": "s", "higher_is_better": False, "cold_s": cold, "speedup": cold / warm,
+            "steps_cold": [r["cold"]["steps"] for r in rows], "steps_warm": [r["warm"]["steps"] for r in rows],
+            "k_rel_diff_max": max(r["k_rel_diff"] for r in rows),
+            "dtype": "f32 LBM, bf16/fp32 network", "data": "synthetic",
+            "config": {"workload": f"{shape[0]}x{shape[1]}x{shape[2]} channels, lower half overlapping r=4 spheres at "
+                                   "porosity U[0.6,0.8]; train seeds 500000+, held-out seeds 600000+",
+                       "train_samples": args.train_samples, "heldout": args.heldout, "epochs": args.epochs},
+            "training": {"data_steps": data.steps, "data_s": data.seconds, "train_s": tr.seconds,
+                         "samples": tr.samples, "loss_first": tr.losses[0], "loss_last": float(np.mean(tr.losses[-8:]))},
+            "rows": rows, "total_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -179,14 +264,26 @@ def run_ours(args, world, rank, local):
 
     if args.workload == "channel":
         cases = [W.W2(phi) for phi in W.W2_POROSITIES]
-    else:   # the same channel at half the size in each direction, for profiler captures
+    elif args.workload == "channel-half":   # the same channel at half the size, for profiler captures
         cases = [W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True,
                            W.W2(phi).seed) for phi in W.W2_POROSITIES]
+    else:   # rev: the periodic REV cubes as one batch
+        cases = [W.W4_cube(i) for i in range(args.cubes)]
     geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
-    solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage) for g, c in zip(geoms, cases)]
+    c0 = cases[0]
+    if args.workload == "rev":
+        solvers = [L.BatchSolver(geoms, c0.tau, c0.lam, c0.g, args.storage)]
+    else:
+        solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage) for g, c in zip(geoms, cases)]
     nfs = [s.info()["n_fluid"] for s in solvers]
     nf_total = sum(nfs)
     lib = L.load_library()
+    # set-up: let the launch-schedule tuner finish its timed trial launches
+    # before the warm-up, so the timed steps use the final schedule
+    for s in solvers:
+        while not s.schedule()["tuned"] and s.steps < 256:
+            s.step(2)
+    schedules = [s.schedule() for s in solvers]
 
     def one_step(events=None):
         for s in solvers:
@@ -246,11 +343,15 @@ def run_ours(args, world, rank, local):
     te = time.perf_counter()
     h2d = 0
     d2h = 0
-    for g, c in zip(geoms, cases):
-        s2 = L.Solver(g, c.tau, c.lam, c.g, args.storage)
+    groups = [geoms] if args.workload == "rev" else [[g] for g in geoms]
+    for grp in groups:
+        if args.workload == "rev":
+            s2 = L.BatchSolver(grp, c0.tau, c0.lam, c0.g, args.storage)
+        else:
+            s2 = L.Solver(grp[0], c0.tau, c0.lam, c0.g, args.storage)
         s2.step(e2e_steps)
         pa = s2.plane_average()
-        h2d += g.mask().nbytes
+        h2d += sum(g.mask().nbytes for g in grp)
         d2h += pa.nbytes
         del s2
     torch.cuda.synchronize()
@@ -261,8 +362,8 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "channel" else WORKLOAD.replace("256x256x512", "128x128x256"),
-                   "fluid_cells": nfs, "storage": args.storage,
+        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage,
+                   "schedule": schedules,
                    "l2": "inputs larger than L2 (4.1-5.7 GB of populations and indices per solver)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -293,14 +394,28 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
-    ap.add_argument("--workload", choices=["channel", "channel-half"], default="channel",
-                    help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for profiling")
+    ap.add_argument("--workload", choices=["channel", "channel-half", "rev", "surrogate"], default="channel",
+                    help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
+                         "profiling; rev: the batched REV cubes")
+    ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
+    ap.add_argument("--converge", action="store_true",
+                    help="instead of timing steps, run to steady state and report the time and permeabilities")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--train-samples", type=int, default=96)
+    ap.add_argument("--heldout", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--interval", type=int, default=500)
+    ap.add_argument("--max-steps", type=int, default=2_000_000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
+    elif args.converge:
+        run_converge(args)
     else:
         run_ours(args, world, rank, local)
 

@@ -79,7 +79,7 @@ _I64 = ctypes.c_int64
 _D = ctypes.c_double
 _SZ = ctypes.c_size_t
 
-# symbol -> (restype, argtypes); every symbol declared in include/lbm.h
+# symbol -> (restype, argtypes); every symbol declared in include/lbm.h and include/unet.h
 SIGNATURES = {
     "lbm_geometry_from_spheres": (_I, [ctypes.POINTER(lbm_sphere_params), ctypes.POINTER(_P)]),
     "lbm_geometry_from_list": (_I, [ctypes.POINTER(lbm_box), _P, _I64, ctypes.POINTER(_P)]),
@@ -113,6 +113,20 @@ SIGNATURES = {
     "lbm_batch_profile_residual": (_I, [_P, _P]),
     "lbm_schedule": (_I, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                           ctypes.POINTER(_I32)]),
+    # include/unet.h
+    "lbm_sdf_workspace_size": (_I, [_P, ctypes.c_float, ctypes.POINTER(_SZ)]),
+    "lbm_sdf": (_I, [_P, ctypes.c_float, _P, _SZ, _P, _P]),
+    "unet_create": (_I, [_I32, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    "unet_destroy": (None, [_P]),
+    "unet_param_count": (_I, [_P, ctypes.POINTER(_I64)]),
+    "unet_workspace_size": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "unet_bind": (_I, [_P, _P, _SZ, _P]),
+    "unet_set_params": (_I, [_P, _P]),
+    "unet_get_params": (_I, [_P, _P]),
+    "unet_get_grads": (_I, [_P, _P]),
+    "unet_forward": (_I, [_P, _P, _P, ctypes.c_float]),
+    "unet_backward": (_I, [_P, _P, ctypes.c_float, ctypes.POINTER(_D)]),
+    "unet_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "lbm_solver_destroy": (None, [_P]),
     "lbm_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -443,6 +457,92 @@ class BatchSolver(Solver):
         out = np.zeros(len(self.geoms), np.float64)
         _check(load_library().lbm_batch_profile_residual(self._h, _np_ptr(out)), "lbm_batch_profile_residual")
         return out
+
+
+def lbm_sdf(geom: Geometry, trunc: float = 8.0, out=None, stream=None):
+    """Truncated signed distance / trunc of a geometry, [nz, ny, nx] float32 on the device."""
+    import torch
+
+    n = _SZ()
+    _check(load_library().lbm_sdf_workspace_size(geom.handle, float(trunc), ctypes.byref(n)),
+           "lbm_sdf_workspace_size")
+    ws = torch.empty(int(n.value), dtype=torch.uint8, device="cuda")
+    if out is None:
+        out = torch.empty(geom.shape, dtype=torch.float32, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load_library().lbm_sdf(geom.handle, float(trunc), _dev_ptr(ws), ws.numel(), _dev_ptr(out),
+                                  ctypes.c_void_p(stream)), "lbm_sdf")
+    return out
+
+
+class UNet:
+    """The warm-start network (include/unet.h) with its device workspace."""
+
+    def __init__(self, n, nz, ny, nx, params=None, stream=None):
+        import torch
+
+        lib = load_library()
+        h = _P()
+        _check(lib.unet_create(int(n), int(nz), int(ny), int(nx), ctypes.byref(h)), "unet_create")
+        self._h = h
+        self.shape = (int(n), int(nz), int(ny), int(nx))
+        cnt, ws = _I64(), _SZ()
+        _check(lib.unet_param_count(h, ctypes.byref(cnt)), "unet_param_count")
+        _check(lib.unet_workspace_size(h, ctypes.byref(ws)), "unet_workspace_size")
+        self.n_params = cnt.value
+        self.workspace = torch.empty(int(ws.value), dtype=torch.uint8, device="cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        _check(lib.unet_bind(h, _dev_ptr(self.workspace), self.workspace.numel(), ctypes.c_void_p(stream)),
+               "unet_bind")
+        if params is not None:
+            self.set_params(params)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            load_library().unet_destroy(self._h)
+            self._h = None
+
+    def set_params(self, params):
+        import torch
+
+        t = torch.as_tensor(params, dtype=torch.float32).contiguous().cuda()
+        assert t.numel() == self.n_params
+        _check(load_library().unet_set_params(self._h, _dev_ptr(t)), "unet_set_params")
+
+    def params(self):
+        import torch
+
+        t = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(load_library().unet_get_params(self._h, _dev_ptr(t)), "unet_get_params")
+        return t
+
+    def grads(self):
+        import torch
+
+        t = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(load_library().unet_get_grads(self._h, _dev_ptr(t)), "unet_get_grads")
+        return t
+
+    def forward(self, sdf, out=None, out_scale=1.0):
+        import torch
+
+        n, nz, ny, nx = self.shape
+        if out is None:
+            out = torch.empty((n, 3, nz, ny, nx), dtype=torch.float32, device="cuda")
+        _check(load_library().unet_forward(self._h, _dev_ptr(sdf), _dev_ptr(out), float(out_scale)), "unet_forward")
+        return out
+
+    def backward(self, target, target_scale=1.0) -> float:
+        loss = _D()
+        _check(load_library().unet_backward(self._h, _dev_ptr(target), float(target_scale), ctypes.byref(loss)),
+               "unet_backward")
+        return loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(load_library().unet_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps)),
+               "unet_adam_step")
 
 
 def lbm_batch_init(geoms, **kw) -> BatchSolver:

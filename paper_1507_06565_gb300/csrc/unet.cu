@@ -1,0 +1,745 @@
+// unet.cu -- a 3-D convolutional U-Net that maps the signed-distance field of
+// a geometry to its steady velocity field, used to warm-start the LBM
+// (Eq. (equilibrium) evaluated at the predicted u0).  The paper has no learned
+// component; the converged LBM stays the judge of the prediction's error.
+//
+// Architecture (fixed): 4 levels of two 3x3x3 convolutions + ReLU with
+// 16/32/64/128 channels, 2x2x2 average pooling, nearest x2 upsampling with the
+// upsampled tensor and the skip tensor concatenated (in that order), and a
+// 1x1x1 head to the 3 velocity components.  Convolutions pad circularly in x
+// and y (the periodic directions) and with zeros in z (the walls).  Input
+// channels: [sdf, z feature in [-1,1], 14 zeros].
+//
+// Numerics: activations, activation gradients and the working copies of the
+// weights are bf16 (layout [voxel][channel]); every contraction accumulates in
+// fp32 on the tensor cores (mma.sync m16n8k16, bf16 inputs); master weights,
+// weight gradients and the Adam moments are fp32.  The 3x3x3 convolution is an
+// implicit GEMM: M = voxels, N = output channels, K = 27 taps x input
+// channels; its backward with respect to the input is the same kernel with
+// the weights flipped in the taps and transposed in the channels (the adjoint
+// of a circular/zero-padded convolution); the weight gradient contracts over
+// voxels with the tensor cores and adds block partials atomically.
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace unet {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kTaps = 27;
+constexpr int kIn = 16;       // input channels after padding
+constexpr int kOut = 3;       // velocity components
+constexpr int kW[4] = {16, 32, 64, 128};   // host-side channel widths
+constexpr int kW0 = 16;                      // first level (used in device code)
+
+// ---------------------------------------------------------------------------
+// tensor-core primitive
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+struct Dims {
+    int n, d, h, w;
+    __host__ __device__ int64_t voxels() const { return (int64_t)n * d * h * w; }
+};
+
+// Voxel v shifted by tap t (dz, dy, dx = t/9-1, t/3%3-1, t%3-1): circular in
+// y and x, -1 when z leaves the box.
+__device__ __forceinline__ int64_t tap_neighbour(const Dims &g, int64_t v, int t)
+{
+    const int x = (int)(v % g.w);
+    int64_t r = v / g.w;
+    const int y = (int)(r % g.h);
+    r /= g.h;
+    const int z = (int)(r % g.d);
+    const int64_t n = r / g.d;
+    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const int zz = z + dz;
+    if (zz < 0 || zz >= g.d) return -1;
+    int yy = y + dy, xx = x + dx;
+    yy = yy < 0 ? yy + g.h : (yy >= g.h ? yy - g.h : yy);
+    xx = xx < 0 ? xx + g.w : (xx >= g.w ? xx - g.w : xx);
+    return ((n * g.d + zz) * g.h + yy) * g.w + xx;
+}
+
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution as implicit GEMM (forward, and backward w.r.t. the input)
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+    const bf16 *in0;
+    int ci0;            // channels of in0 (multiple of 16)
+    const bf16 *in1;
+    int ci1;            // channels of in1 (0: none); the input is [in0, in1]
+    const bf16 *w;      // [27][co][ci]
+    const float *bias;  // [co] or null
+    bf16 *out0;
+    int co0;            // output channels [0, co0) -> out0 (row length co0)
+    bf16 *out1;
+    int co1;            // [co0, co0 + co1) -> out1 (row length co1)
+    int relu;
+    Dims g;
+};
+
+constexpr int kConvBM = 64;        // voxels per block (4 warps x 16 rows)
+constexpr int kPadK = 24;          // smem row length in bf16 (16 + 8 padding: conflict-free fragments)
+
+template <int BN>
+__global__ void __launch_bounds__(128) k_conv3(ConvArgs a)
+{
+    __shared__ __align__(16) bf16 As[kConvBM][kPadK];
+    __shared__ __align__(16) bf16 Bs[BN][kPadK];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+    const int64_t m0 = (int64_t)blockIdx.x * kConvBM;
+    const int n0 = blockIdx.y * BN;
+    const int ci = a.ci0 + a.ci1, co = a.co0 + a.co1;
+    const int64_t V = a.g.voxels();
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+    // the A row this thread stages (two threads per row, 8 channels each)
+    const int arow = tid >> 1, ahalf = tid & 1;
+    const int64_t av = m0 + arow;
+    for (int t = 0; t < kTaps; ++t) {
+        const int64_t nb = av < V ? tap_neighbour(a.g, av, t) : -1;
+        for (int c0 = 0; c0 < ci; c0 += 16) {
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (nb >= 0) {
+                const bf16 *src = c0 < a.ci0 ? a.in0 + nb * a.ci0 + c0 : a.in1 + nb * a.ci1 + (c0 - a.ci0);
+                val = *reinterpret_cast<const uint4 *>(src + ahalf * 8);
+            }
+            *reinterpret_cast<uint4 *>(&As[arow][ahalf * 8]) = val;
+            if (tid < 2 * BN) {
+                const int brow = tid >> 1, bhalf = tid & 1;
+                uint4 wv = make_uint4(0u, 0u, 0u, 0u);
+                if (n0 + brow < co)
+                    wv = *reinterpret_cast<const uint4 *>(a.w + ((int64_t)t * co + n0 + brow) * ci + c0 + bhalf * 8);
+                *reinterpret_cast<uint4 *>(&Bs[brow][bhalf * 8]) = wv;
+            }
+            __syncthreads();
+            uint32_t af[4];
+            const int r = warp * 16 + g;
+            af[0] = *reinterpret_cast<const uint32_t *>(&As[r][2 * t4]);
+            af[1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * t4]);
+            af[2] = *reinterpret_cast<const uint32_t *>(&As[r][2 * t4 + 8]);
+            af[3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * t4 + 8]);
+#pragma unroll
+            for (int j = 0; j < BN / 8; ++j) {
+                uint32_t bfr[2];
+                bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[8 * j + g][2 * t4]);
+                bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[8 * j + g][2 * t4 + 8]);
+                mma_bf16(acc[j], af, bfr);
+            }
+            __syncthreads();
+        }
+    }
+    // epilogue: bias, ReLU, bf16 pairs to the output channel range
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+        const int c = n0 + 8 * j + 2 * t4;
+        if (c >= co) continue;
+        const float b0 = a.bias ? a.bias[c] : 0.0f, b1 = a.bias ? a.bias[c + 1] : 0.0f;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int64_t v = m0 + warp * 16 + g + 8 * half;
+            if (v >= V) continue;
+            float y0 = acc[j][2 * half] + b0, y1 = acc[j][2 * half + 1] + b1;
+            if (a.relu) {
+                y0 = fmaxf(y0, 0.0f);
+                y1 = fmaxf(y1, 0.0f);
+            }
+            const __nv_bfloat162 pr = __floats2bfloat162_rn(y0, y1);
+            bf16 *dst = c < a.co0 ? a.out0 + v * a.co0 + c : a.out1 + v * a.co1 + (c - a.co0);
+            *reinterpret_cast<__nv_bfloat162 *>(dst) = pr;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient: dW[t][o][c] += sum_v dY[v][o] X(v + off_t)[c]
+// (M = output channels, N = 16 input channels per block, K = voxels)
+// ---------------------------------------------------------------------------
+struct WgradArgs {
+    const bf16 *dy;
+    int co;
+    const bf16 *in0;
+    int ci0;
+    const bf16 *in1;
+    int ci1;
+    float *dw;          // [27][co][ci] fp32 (accumulated)
+    Dims g;
+    int chunk;          // voxels per block
+};
+
+template <int BM>
+__global__ void __launch_bounds__(32 * (BM / 16)) k_wgrad(WgradArgs a)
+{
+    __shared__ __align__(16) bf16 Ys[16][BM + 8];
+    __shared__ __align__(16) bf16 Xs[16][kPadK];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
+    const int nthreads = 32 * (BM / 16);
+    const int o0 = blockIdx.y * BM, c0 = blockIdx.z * 16;
+    const int t = (int)(blockIdx.x % kTaps);
+    const int64_t v_begin = (int64_t)(blockIdx.x / kTaps) * a.chunk;
+    const int64_t V = a.g.voxels();
+    const int64_t v_end = v_begin + a.chunk < V ? v_begin + a.chunk : V;
+    const int ci = a.ci0 + a.ci1;
+    float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    for (int64_t vb = v_begin; vb < v_end; vb += 16) {
+        // stage dY[vb..vb+16][o0..o0+BM] and X(v + off)[c0..c0+16]
+        for (int e = tid; e < 16 * (BM / 8); e += nthreads) {
+            const int r = e / (BM / 8), q = e % (BM / 8);
+            const int64_t v = vb + r;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (v < v_end && o0 + 8 * q < a.co) val = *reinterpret_cast<const uint4 *>(a.dy + v * a.co + o0 + 8 * q);
+            *reinterpret_cast<uint4 *>(&Ys[r][8 * q]) = val;
+        }
+        if (tid < 32) {
+            const int r = tid >> 1, half = tid & 1;
+            const int64_t v = vb + r;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (v < v_end) {
+                const int64_t nb = tap_neighbour(a.g, v, t);
+                if (nb >= 0) {
+                    const bf16 *src = c0 < a.ci0 ? a.in0 + nb * a.ci0 + c0 : a.in1 + nb * a.ci1 + (c0 - a.ci0);
+                    val = *reinterpret_cast<const uint4 *>(src + 8 * half);
+                }
+            }
+            *reinterpret_cast<uint4 *>(&Xs[r][8 * half]) = val;
+        }
+        __syncthreads();
+        // A (rows o, cols v) = Ys[v][o]; B (rows v, cols c) = Xs[v][c]
+        const int o = warp * 16 + g;
+        uint32_t af[4];
+        af[0] = pack2(Ys[2 * t4][o], Ys[2 * t4 + 1][o]);
+        af[1] = pack2(Ys[2 * t4][o + 8], Ys[2 * t4 + 1][o + 8]);
+        af[2] = pack2(Ys[2 * t4 + 8][o], Ys[2 * t4 + 9][o]);
+        af[3] = pack2(Ys[2 * t4 + 8][o + 8], Ys[2 * t4 + 9][o + 8]);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            uint32_t bfr[2];
+            bfr[0] = pack2(Xs[2 * t4][8 * j + g], Xs[2 * t4 + 1][8 * j + g]);
+            bfr[1] = pack2(Xs[2 * t4 + 8][8 * j + g], Xs[2 * t4 + 9][8 * j + g]);
+            mma_bf16(acc[j], af, bfr);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int o = o0 + warp * 16 + g + 8 * (e >> 1);
+            const int c = c0 + 8 * j + 2 * t4 + (e & 1);
+            if (o < a.co && c < ci) atomicAdd(a.dw + ((int64_t)t * a.co + o) * ci + c, acc[j][e]);
+        }
+}
+
+// bias gradient: db[o] += sum_v dY[v][o]
+__global__ void k_bias_grad(const bf16 *__restrict__ dy, int co, int64_t V, float *__restrict__ db)
+{
+    extern __shared__ float part[];
+    const int o = threadIdx.x % co, lanes = blockDim.x / co, l = threadIdx.x / co;
+    float s = 0.0f;
+    if (threadIdx.x < lanes * co)
+        for (int64_t v = (int64_t)blockIdx.x * lanes + l; v < V; v += (int64_t)gridDim.x * lanes)
+            s += __bfloat162float(dy[v * co + o]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < co) {
+        float tot = 0.0f;
+        for (int k = 0; k < lanes; ++k) tot += part[k * co + threadIdx.x];
+        atomicAdd(db + threadIdx.x, tot);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise pieces
+// ---------------------------------------------------------------------------
+// input channels [sdf, z feature, zeros] as bf16 [voxel][16]
+__global__ void k_make_input(const float *__restrict__ sdf, Dims g, bf16 *__restrict__ x)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.voxels()) return;
+    const int z = (int)((v / ((int64_t)g.w * g.h)) % g.d);
+    const float zf = g.d > 1 ? -1.0f + 2.0f * (float)z / (float)(g.d - 1) : 0.0f;
+    bf16 *row = x + v * kIn;
+    row[0] = __float2bfloat16_rn(sdf[v]);
+    row[1] = __float2bfloat16_rn(zf);
+    for (int c = 2; c < kIn; ++c) row[c] = __float2bfloat16_rn(0.0f);
+}
+
+// out = scale * sum of the 8 children (2x2x2 average pooling with scale 1/8)
+__global__ void k_pool(const bf16 *__restrict__ in, Dims gi, int c, float scale, bf16 *__restrict__ out)
+{
+    const Dims go{gi.n, gi.d / 2, gi.h / 2, gi.w / 2};
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= go.voxels() * c) return;
+    const int ch = (int)(e % c);
+    int64_t v = e / c;
+    const int x = (int)(v % go.w);
+    v /= go.w;
+    const int y = (int)(v % go.h);
+    v /= go.h;
+    const int z = (int)(v % go.d);
+    const int64_t n = v / go.d;
+    float s = 0.0f;
+    for (int k = 0; k < 8; ++k) {
+        const int64_t vi = ((n * gi.d + 2 * z + (k >> 2)) * gi.h + 2 * y + ((k >> 1) & 1)) * gi.w + 2 * x + (k & 1);
+        s += __bfloat162float(in[vi * c + ch]);
+    }
+    out[e] = __float2bfloat16_rn(scale * s);
+}
+
+// out (+)= scale * parent (nearest-neighbour x2 upsampling)
+__global__ void k_upsample(const bf16 *__restrict__ in, Dims go, int c, float scale, int accumulate,
+                           bf16 *__restrict__ out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= go.voxels() * c) return;
+    const int ch = (int)(e % c);
+    int64_t v = e / c;
+    const int x = (int)(v % go.w);
+    v /= go.w;
+    const int y = (int)(v % go.h);
+    v /= go.h;
+    const int z = (int)(v % go.d);
+    const int64_t n = v / go.d;
+    const Dims gi{go.n, go.d / 2, go.h / 2, go.w / 2};
+    const int64_t vi = ((n * gi.d + z / 2) * gi.h + y / 2) * gi.w + x / 2;
+    float r = scale * __bfloat162float(in[vi * c + ch]);
+    if (accumulate) r += __bfloat162float(out[e]);
+    out[e] = __float2bfloat16_rn(r);
+}
+
+// dy *= (y > 0)
+__global__ void k_relu_back(bf16 *__restrict__ dy, const bf16 *__restrict__ y, int64_t n)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n && !(__bfloat162float(y[e]) > 0.0f)) dy[e] = __float2bfloat16_rn(0.0f);
+}
+
+// head: out[v][o] = b[o] + sum_c W[o][c] x[v][c]; writes the normalised output
+// (fp32 [voxel][3]) and scale * output in the LBM layout [n][3][nz][ny][nx]
+__global__ void k_head(const bf16 *__restrict__ x, const float *__restrict__ w, const float *__restrict__ b, Dims g,
+                       float scale, float *__restrict__ out_norm, float *__restrict__ out_field)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.voxels()) return;
+    const int64_t per = (int64_t)g.d * g.h * g.w;
+    const int64_t n = v / per, cell = v % per;
+    for (int o = 0; o < kOut; ++o) {
+        float s = b[o];
+        for (int c = 0; c < kW0; ++c) s += __bfloat162float(__float2bfloat16_rn(w[o * kW0 + c])) * __bfloat162float(x[v * kW0 + c]);
+        out_norm[v * kOut + o] = s;
+        if (out_field) out_field[(n * kOut + o) * per + cell] = scale * s;
+    }
+}
+
+// loss and head backward: dout = 2 (out - tscale * target) / (3 V);
+// dx[v][c] = sum_o W[o][c] dout[v][o]; head weight/bias gradients and the
+// loss (sum of squares) accumulate per block.
+__global__ void k_head_back(const bf16 *__restrict__ x, const float *__restrict__ w, const float *__restrict__ out_norm,
+                            const float *__restrict__ target, float tscale, Dims g, bf16 *__restrict__ dx,
+                            float *__restrict__ dw, float *__restrict__ db, double *__restrict__ loss)
+{
+    __shared__ float sw[kOut * 16 + kOut];
+    __shared__ double sl;
+    if (threadIdx.x < kOut * 16 + kOut) sw[threadIdx.x] = 0.0f;
+    if (threadIdx.x == 0) sl = 0.0;
+    __syncthreads();
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t V = g.voxels();
+    if (v < V) {
+        const int64_t per = (int64_t)g.d * g.h * g.w;
+        const int64_t n = v / per, cell = v % per;
+        float d[kOut];
+        double l = 0.0;
+        for (int o = 0; o < kOut; ++o) {
+            const float diff = out_norm[v * kOut + o] - tscale * target[(n * kOut + o) * per + cell];
+            l += (double)diff * diff;
+            d[o] = 2.0f * diff / (float)(kOut * V);
+        }
+        atomicAdd(&sl, l);
+        for (int c = 0; c < 16; ++c) {
+            const float xc = __bfloat162float(x[v * 16 + c]);
+            float s = 0.0f;
+            for (int o = 0; o < kOut; ++o) {
+                s += __bfloat162float(__float2bfloat16_rn(w[o * 16 + c])) * d[o];
+                atomicAdd(&sw[o * 16 + c], d[o] * xc);
+            }
+            dx[v * 16 + c] = __float2bfloat16_rn(s);
+        }
+        for (int o = 0; o < kOut; ++o) atomicAdd(&sw[kOut * 16 + o], d[o]);
+    }
+    __syncthreads();
+    if (threadIdx.x < kOut * 16) atomicAdd(dw + threadIdx.x, sw[threadIdx.x]);
+    else if (threadIdx.x < kOut * 16 + kOut) atomicAdd(db + threadIdx.x - kOut * 16, sw[threadIdx.x]);
+    if (threadIdx.x == 0) atomicAdd(loss, sl);
+}
+
+// fp32 master weights -> bf16 working copies: forward [t][o][c] and the
+// backward-data layout [t][c][o] flipped in the taps (t -> 26 - t)
+__global__ void k_weights_bf16(const float *__restrict__ w, int co, int ci, bf16 *__restrict__ wf, bf16 *__restrict__ wb)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)kTaps * co * ci) return;
+    const int c = (int)(e % ci);
+    const int o = (int)((e / ci) % co);
+    const int t = (int)(e / ((int64_t)ci * co));
+    const bf16 v = __float2bfloat16_rn(w[e]);
+    wf[e] = v;
+    wb[((int64_t)(kTaps - 1 - t) * ci + c) * co + o] = v;
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ gr, float *__restrict__ m, float *__restrict__ v,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float gi = gr[e];
+    const float mi = b1 * m[e] + (1.0f - b1) * gi;
+    const float vi = b2 * v[e] + (1.0f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Layer {
+    int co, ci;
+    int64_t w_off, b_off;   // offsets (floats) in the flat parameter vector
+    bf16 *wf = nullptr, *wb = nullptr;
+};
+
+enum { ENC1A, ENC1B, ENC2A, ENC2B, ENC3A, ENC3B, BOTTA, BOTTB, DEC3A, DEC3B, DEC2A, DEC2B, DEC1A, DEC1B, NLAYERS };
+
+struct Net {
+    Dims g[4];                     // dims per level
+    std::vector<Layer> layers;
+    int64_t head_w = 0, head_b = 0, n_params = 0;
+    cudaStream_t st = nullptr;
+    char *ws = nullptr;
+    size_t ws_need = 0;
+    int64_t adam_t = 0;
+    // fp32 buffers
+    float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+    float *out_norm = nullptr;
+    double *loss = nullptr;
+    // activations (bf16) and their gradients
+    bf16 *in = nullptr;
+    bf16 *act[NLAYERS] = {};
+    bf16 *dact[NLAYERS] = {};
+    bf16 *p1 = nullptr, *p2 = nullptr, *p3 = nullptr, *dp1 = nullptr, *dp2 = nullptr, *dp3 = nullptr;
+    bf16 *u1 = nullptr, *u2 = nullptr, *u3 = nullptr, *du1 = nullptr, *du2 = nullptr, *du3 = nullptr;
+};
+
+static int64_t layout(Net &net, bool assign)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = lbm::align_up(off + (bytes ? bytes : 1), 256);
+        return assign ? net.ws + at : nullptr;
+    };
+    const int64_t P = net.n_params;
+    net.params = (float *)take(P * 4);
+    net.grads = (float *)take(P * 4);
+    net.m = (float *)take(P * 4);
+    net.v = (float *)take(P * 4);
+    for (Layer &L : net.layers) {
+        L.wf = (bf16 *)take((size_t)kTaps * L.co * L.ci * 2);
+        L.wb = (bf16 *)take((size_t)kTaps * L.co * L.ci * 2);
+    }
+    net.out_norm = (float *)take((size_t)net.g[0].voxels() * kOut * 4);
+    net.loss = (double *)take(8);
+    const int lvl[NLAYERS] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
+    net.in = (bf16 *)take((size_t)net.g[0].voxels() * kIn * 2);
+    for (int l = 0; l < NLAYERS; ++l) {
+        const size_t b = (size_t)net.g[lvl[l]].voxels() * net.layers[l].co * 2;
+        net.act[l] = (bf16 *)take(b);
+        net.dact[l] = (bf16 *)take(b);
+    }
+    net.p1 = (bf16 *)take((size_t)net.g[1].voxels() * kW[0] * 2);
+    net.dp1 = (bf16 *)take((size_t)net.g[1].voxels() * kW[0] * 2);
+    net.p2 = (bf16 *)take((size_t)net.g[2].voxels() * kW[1] * 2);
+    net.dp2 = (bf16 *)take((size_t)net.g[2].voxels() * kW[1] * 2);
+    net.p3 = (bf16 *)take((size_t)net.g[3].voxels() * kW[2] * 2);
+    net.dp3 = (bf16 *)take((size_t)net.g[3].voxels() * kW[2] * 2);
+    net.u3 = (bf16 *)take((size_t)net.g[2].voxels() * kW[3] * 2);
+    net.du3 = (bf16 *)take((size_t)net.g[2].voxels() * kW[3] * 2);
+    net.u2 = (bf16 *)take((size_t)net.g[1].voxels() * kW[2] * 2);
+    net.du2 = (bf16 *)take((size_t)net.g[1].voxels() * kW[2] * 2);
+    net.u1 = (bf16 *)take((size_t)net.g[0].voxels() * kW[1] * 2);
+    net.du1 = (bf16 *)take((size_t)net.g[0].voxels() * kW[1] * 2);
+    return (int64_t)off;
+}
+
+static unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+#define UNET_TRY(x)                                    \
+    do {                                               \
+        if ((x) != cudaSuccess) return LBM_ECUDA;      \
+    } while (0)
+
+// N tile: the largest of 64, 32, 16 that divides the output channel count
+// (16, 32, 48, 64, 96, 128 or 192); the grid covers co / BN tiles.
+static void launch_conv(const ConvArgs &a, cudaStream_t st)
+{
+    const int co = a.co0 + a.co1;
+    const unsigned gx = blocks(a.g.voxels(), kConvBM);
+    if (co % 64 == 0) k_conv3<64><<<dim3(gx, (unsigned)(co / 64)), 128, 0, st>>>(a);
+    else if (co % 32 == 0) k_conv3<32><<<dim3(gx, (unsigned)(co / 32)), 128, 0, st>>>(a);
+    else k_conv3<16><<<dim3(gx, (unsigned)(co / 16)), 128, 0, st>>>(a);
+}
+
+static int conv(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1, int ci1, const Dims &g)
+{
+    const Layer &L = net.layers[l];
+    ConvArgs a{in0, ci0, in1, ci1, L.wf, net.params + L.b_off, net.act[l], L.co, nullptr, 0, 1, g};
+    launch_conv(a, net.st);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+// backward of conv layer l: mask by ReLU, weight/bias gradients, and (unless
+// dx0 is null) the input gradient split into [dx0 (ci0), dx1 (ci1)]
+static int conv_back(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1, int ci1, bf16 *dx0, bf16 *dx1,
+                     const Dims &g)
+{
+    Layer &L = net.layers[l];
+    const int64_t V = g.voxels();
+    k_relu_back<<<blocks(V * L.co), 256, 0, net.st>>>(net.dact[l], net.act[l], V * L.co);
+    // weight gradient: grid x = (voxel chunk, tap), y = output-channel tile,
+    // z = input-channel tile (x has no 65535 limit; y, z stay below 16)
+    const int chunk = 512;
+    WgradArgs wa{net.dact[l], L.co, in0, ci0, in1, ci1, net.grads + L.w_off, g, chunk};
+    const unsigned nchunk = blocks(V, chunk);
+    const unsigned cit = (unsigned)((ci0 + ci1) / 16);
+    if (L.co >= 64) {
+        k_wgrad<64><<<dim3(nchunk * kTaps, (unsigned)(L.co / 64), cit), 128, 0, net.st>>>(wa);
+    } else if (L.co == 32) {
+        k_wgrad<32><<<dim3(nchunk * kTaps, 1, cit), 64, 0, net.st>>>(wa);
+    } else {
+        k_wgrad<16><<<dim3(nchunk * kTaps, 1, cit), 32, 0, net.st>>>(wa);
+    }
+    const int lanes = 256 / L.co;
+    k_bias_grad<<<(unsigned)std::min<int64_t>(1024, blocks(V, lanes)), lanes * L.co, lanes * L.co * 4, net.st>>>(
+        net.dact[l], L.co, V, net.grads + L.b_off);
+    if (dx0) {
+        // input gradient: the forward kernel with flipped, transposed weights
+        ConvArgs a{net.dact[l], L.co, nullptr, 0, L.wb, nullptr, dx0, ci0, dx1, ci1, 0, g};
+        launch_conv(a, net.st);
+    }
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+static int refresh_weights(Net &net)
+{
+    for (const Layer &L : net.layers)
+        k_weights_bf16<<<blocks((int64_t)kTaps * L.co * L.ci), 256, 0, net.st>>>(net.params + L.w_off, L.co, L.ci, L.wf,
+                                                                                L.wb);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+static int forward(Net &net, const float *sdf, float *out, float scale)
+{
+    const Dims *g = net.g;
+    k_make_input<<<blocks(g[0].voxels()), 256, 0, net.st>>>(sdf, g[0], net.in);
+    int rc = conv(net, ENC1A, net.in, kIn, nullptr, 0, g[0]);
+    rc |= conv(net, ENC1B, net.act[ENC1A], kW[0], nullptr, 0, g[0]);
+    k_pool<<<blocks(g[1].voxels() * kW[0]), 256, 0, net.st>>>(net.act[ENC1B], g[0], kW[0], 0.125f, net.p1);
+    rc |= conv(net, ENC2A, net.p1, kW[0], nullptr, 0, g[1]);
+    rc |= conv(net, ENC2B, net.act[ENC2A], kW[1], nullptr, 0, g[1]);
+    k_pool<<<blocks(g[2].voxels() * kW[1]), 256, 0, net.st>>>(net.act[ENC2B], g[1], kW[1], 0.125f, net.p2);
+    rc |= conv(net, ENC3A, net.p2, kW[1], nullptr, 0, g[2]);
+    rc |= conv(net, ENC3B, net.act[ENC3A], kW[2], nullptr, 0, g[2]);
+    k_pool<<<blocks(g[3].voxels() * kW[2]), 256, 0, net.st>>>(net.act[ENC3B], g[2], kW[2], 0.125f, net.p3);
+    rc |= conv(net, BOTTA, net.p3, kW[2], nullptr, 0, g[3]);
+    rc |= conv(net, BOTTB, net.act[BOTTA], kW[3], nullptr, 0, g[3]);
+    k_upsample<<<blocks(g[2].voxels() * kW[3]), 256, 0, net.st>>>(net.act[BOTTB], g[2], kW[3], 1.0f, 0, net.u3);
+    rc |= conv(net, DEC3A, net.u3, kW[3], net.act[ENC3B], kW[2], g[2]);
+    rc |= conv(net, DEC3B, net.act[DEC3A], kW[2], nullptr, 0, g[2]);
+    k_upsample<<<blocks(g[1].voxels() * kW[2]), 256, 0, net.st>>>(net.act[DEC3B], g[1], kW[2], 1.0f, 0, net.u2);
+    rc |= conv(net, DEC2A, net.u2, kW[2], net.act[ENC2B], kW[1], g[1]);
+    rc |= conv(net, DEC2B, net.act[DEC2A], kW[1], nullptr, 0, g[1]);
+    k_upsample<<<blocks(g[0].voxels() * kW[1]), 256, 0, net.st>>>(net.act[DEC2B], g[0], kW[1], 1.0f, 0, net.u1);
+    rc |= conv(net, DEC1A, net.u1, kW[1], net.act[ENC1B], kW[0], g[0]);
+    rc |= conv(net, DEC1B, net.act[DEC1A], kW[0], nullptr, 0, g[0]);
+    k_head<<<blocks(g[0].voxels()), 256, 0, net.st>>>(net.act[DEC1B], net.params + net.head_w, net.params + net.head_b,
+                                                      g[0], scale, net.out_norm, out);
+    if (rc != LBM_OK) return LBM_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+static int backward(Net &net, const float *target, float tscale)
+{
+    const Dims *g = net.g;
+    UNET_TRY(cudaMemsetAsync(net.grads, 0, net.n_params * 4, net.st));
+    UNET_TRY(cudaMemsetAsync(net.loss, 0, 8, net.st));
+    k_head_back<<<blocks(g[0].voxels()), 256, 0, net.st>>>(net.act[DEC1B], net.params + net.head_w, net.out_norm,
+                                                           target, tscale, g[0], net.dact[DEC1B], net.grads + net.head_w,
+                                                           net.grads + net.head_b, net.loss);
+    int rc = conv_back(net, DEC1B, net.act[DEC1A], kW[0], nullptr, 0, net.dact[DEC1A], nullptr, g[0]);
+    rc |= conv_back(net, DEC1A, net.u1, kW[1], net.act[ENC1B], kW[0], net.du1, net.dact[ENC1B], g[0]);
+    k_pool<<<blocks(g[1].voxels() * kW[1]), 256, 0, net.st>>>(net.du1, g[0], kW[1], 1.0f, net.dact[DEC2B]);
+    rc |= conv_back(net, DEC2B, net.act[DEC2A], kW[1], nullptr, 0, net.dact[DEC2A], nullptr, g[1]);
+    rc |= conv_back(net, DEC2A, net.u2, kW[2], net.act[ENC2B], kW[1], net.du2, net.dact[ENC2B], g[1]);
+    k_pool<<<blocks(g[2].voxels() * kW[2]), 256, 0, net.st>>>(net.du2, g[1], kW[2], 1.0f, net.dact[DEC3B]);
+    rc |= conv_back(net, DEC3B, net.act[DEC3A], kW[2], nullptr, 0, net.dact[DEC3A], nullptr, g[2]);
+    rc |= conv_back(net, DEC3A, net.u3, kW[3], net.act[ENC3B], kW[2], net.du3, net.dact[ENC3B], g[2]);
+    k_pool<<<blocks(g[3].voxels() * kW[3]), 256, 0, net.st>>>(net.du3, g[2], kW[3], 1.0f, net.dact[BOTTB]);
+    rc |= conv_back(net, BOTTB, net.act[BOTTA], kW[3], nullptr, 0, net.dact[BOTTA], nullptr, g[3]);
+    rc |= conv_back(net, BOTTA, net.p3, kW[2], nullptr, 0, net.dp3, nullptr, g[3]);
+    k_upsample<<<blocks(g[2].voxels() * kW[2]), 256, 0, net.st>>>(net.dp3, g[2], kW[2], 0.125f, 1, net.dact[ENC3B]);
+    rc |= conv_back(net, ENC3B, net.act[ENC3A], kW[2], nullptr, 0, net.dact[ENC3A], nullptr, g[2]);
+    rc |= conv_back(net, ENC3A, net.p2, kW[1], nullptr, 0, net.dp2, nullptr, g[2]);
+    k_upsample<<<blocks(g[1].voxels() * kW[1]), 256, 0, net.st>>>(net.dp2, g[1], kW[1], 0.125f, 1, net.dact[ENC2B]);
+    rc |= conv_back(net, ENC2B, net.act[ENC2A], kW[1], nullptr, 0, net.dact[ENC2A], nullptr, g[1]);
+    rc |= conv_back(net, ENC2A, net.p1, kW[0], nullptr, 0, net.dp1, nullptr, g[1]);
+    k_upsample<<<blocks(g[0].voxels() * kW[0]), 256, 0, net.st>>>(net.dp1, g[0], kW[0], 0.125f, 1, net.dact[ENC1B]);
+    rc |= conv_back(net, ENC1B, net.act[ENC1A], kW[0], nullptr, 0, net.dact[ENC1A], nullptr, g[0]);
+    rc |= conv_back(net, ENC1A, net.in, kIn, nullptr, 0, nullptr, nullptr, g[0]);
+    if (rc != LBM_OK) return LBM_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+}  // namespace unet
+
+struct unet_net : public unet::Net {};
+
+using namespace unet;
+
+extern "C" {
+
+int unet_create(int32_t n, int32_t nz, int32_t ny, int32_t nx, unet_net **out)
+{
+    if (!out || n < 1 || nz < 8 || ny < 8 || nx < 8 || nz % 8 || ny % 8 || nx % 8) return LBM_EINVAL;
+    if ((int64_t)n * nz * ny * nx >= ((int64_t)1 << 31)) return LBM_EINVAL;
+    unet_net *net = new (std::nothrow) unet_net();
+    if (!net) return LBM_ENOMEM;
+    for (int l = 0; l < 4; ++l) net->g[l] = Dims{n, nz >> l, ny >> l, nx >> l};
+    const int shapes[NLAYERS][2] = {{kW[0], kIn},          {kW[0], kW[0]}, {kW[1], kW[0]},         {kW[1], kW[1]},
+                                    {kW[2], kW[1]},        {kW[2], kW[2]}, {kW[3], kW[2]},         {kW[3], kW[3]},
+                                    {kW[2], kW[3] + kW[2]}, {kW[2], kW[2]}, {kW[1], kW[2] + kW[1]}, {kW[1], kW[1]},
+                                    {kW[0], kW[1] + kW[0]}, {kW[0], kW[0]}};
+    int64_t off = 0;
+    for (int l = 0; l < NLAYERS; ++l) {
+        Layer L;
+        L.co = shapes[l][0];
+        L.ci = shapes[l][1];
+        L.w_off = off;
+        off += (int64_t)kTaps * L.co * L.ci;
+        L.b_off = off;
+        off += L.co;
+        net->layers.push_back(L);
+    }
+    net->head_w = off;
+    off += kOut * kW[0];
+    net->head_b = off;
+    off += kOut;
+    net->n_params = off;
+    net->ws_need = (size_t)layout(*net, false);
+    *out = net;
+    return LBM_OK;
+}
+
+int unet_param_count(const unet_net *net, int64_t *n)
+{
+    if (!net || !n) return LBM_EINVAL;
+    *n = net->n_params;
+    return LBM_OK;
+}
+
+int unet_workspace_size(const unet_net *net, size_t *bytes)
+{
+    if (!net || !bytes) return LBM_EINVAL;
+    *bytes = net->ws_need;
+    return LBM_OK;
+}
+
+int unet_bind(unet_net *net, void *dev_ws, size_t bytes, void *stream)
+{
+    if (!net || !dev_ws || ((uintptr_t)dev_ws & 255u)) return LBM_EINVAL;
+    if (bytes < net->ws_need) return LBM_ESIZE;
+    net->ws = (char *)dev_ws;
+    net->st = (cudaStream_t)stream;
+    layout(*net, true);
+    UNET_TRY(cudaMemsetAsync(net->m, 0, net->n_params * 4, net->st));
+    UNET_TRY(cudaMemsetAsync(net->v, 0, net->n_params * 4, net->st));
+    net->adam_t = 0;
+    return LBM_OK;
+}
+
+int unet_set_params(unet_net *net, const float *dev_params)
+{
+    if (!net || !net->ws || !dev_params) return LBM_EINVAL;
+    UNET_TRY(cudaMemcpyAsync(net->params, dev_params, net->n_params * 4, cudaMemcpyDeviceToDevice, net->st));
+    return refresh_weights(*net);
+}
+
+int unet_get_params(unet_net *net, float *dev_params)
+{
+    if (!net || !net->ws || !dev_params) return LBM_EINVAL;
+    UNET_TRY(cudaMemcpyAsync(dev_params, net->params, net->n_params * 4, cudaMemcpyDeviceToDevice, net->st));
+    return LBM_OK;
+}
+
+int unet_get_grads(unet_net *net, float *dev_grads)
+{
+    if (!net || !net->ws || !dev_grads) return LBM_EINVAL;
+    UNET_TRY(cudaMemcpyAsync(dev_grads, net->grads, net->n_params * 4, cudaMemcpyDeviceToDevice, net->st));
+    return LBM_OK;
+}
+
+int unet_forward(unet_net *net, const float *dev_sdf, float *dev_u, float out_scale)
+{
+    if (!net || !net->ws || !dev_sdf) return LBM_EINVAL;
+    return unet::forward(*net, dev_sdf, dev_u, out_scale);
+}
+
+int unet_backward(unet_net *net, const float *dev_target, float target_scale, double *host_loss)
+{
+    if (!net || !net->ws || !dev_target) return LBM_EINVAL;
+    int rc = unet::backward(*net, dev_target, target_scale);
+    if (rc != LBM_OK) return rc;
+    if (host_loss) {
+        double s = 0.0;
+        UNET_TRY(cudaMemcpyAsync(&s, net->loss, 8, cudaMemcpyDeviceToHost, net->st));
+        UNET_TRY(cudaStreamSynchronize(net->st));
+        *host_loss = s / (double)(kOut * net->g[0].voxels());
+    }
+    return LBM_OK;
+}
+
+int unet_adam_step(unet_net *net, float lr, float beta1, float beta2, float eps)
+{
+    if (!net || !net->ws || !(lr > 0.0f)) return LBM_EINVAL;
+    net->adam_t += 1;
+    const float c1 = 1.0f - (float)std::pow((double)beta1, (double)net->adam_t);
+    const float c2 = 1.0f - (float)std::pow((double)beta2, (double)net->adam_t);
+    k_adam<<<blocks(net->n_params), 256, 0, net->st>>>(net->params, net->grads, net->m, net->v, net->n_params, lr, beta1,
+                                                      beta2, eps, c1, c2);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    return refresh_weights(*net);
+}
+
+void unet_destroy(unet_net *net) { delete net; }
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+"""Learned warm start of the LBM: orchestration of the C ABI only.
+
+1. training data: seeded channel packings are run to steady state by the
+   batched solver (one launch per step for all of them); the steady velocity
+   fields are the labels and the truncated signed distances the inputs;
+2. training: the U-Net of include/unet.h, forward/backward/Adam in the
+   library's kernels, on labels scaled by nu / (g (nz/4)^2) (Stokes flow is
+   linear in g / nu);
+3. warm start: the network's prediction, scaled back to lattice units,
+   initialises lbm_init; the LBM then runs to the same steady-state tolerance
+   as a cold start, so the prediction only changes the number of steps, and
+   the converged LBM judges the prediction.
+
+Every arithmetic step runs in the library's kernels; torch only provides
+device memory (reshapes, copies and slices of tensors).
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import BatchSolver, Solver, UNet, lbm_geometry_from_spheres, lbm_sdf
+from .workloads import Channel, unet_init
+
+SDF_TRUNC = 8.0
+
+
+def channel_case(seed: int, shape=(64, 64, 128)) -> Channel:
+    """A walled channel (nx, ny, nz) whose lower half holds overlapping r = 4
+    spheres at a seeded porosity in [0.6, 0.8] (non-overlapping placement
+    cannot reach 0.6 at this radius: the jamming limit is near 0.62)."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    phi = float(np.round(rng.uniform(0.6, 0.8), 6))
+    return Channel(f"channel seed {seed}", nx, ny, nz, 1.0, nz / 2.0, 4.0, 4.0, phi, True, seed)
+
+
+def velocity_scale(case: Channel) -> float:
+    """Lattice velocity per unit network output: g (nz/4)^2 / nu."""
+    nu = (case.tau - 0.5) / 3.0
+    return case.g[0] * (case.nz / 4.0) ** 2 / nu
+
+
+@dataclass
+class Dataset:
+    sdf: object       # torch [N, nz, ny, nx]
+    u: object         # torch [N, 3, nz, ny, nx]
+    cases: list
+    steps: int
+    seconds: float
+
+
+def generate(seeds, shape=(64, 64, 128), tol=1e-6, interval=500, max_steps=400_000) -> Dataset:
+    """Steady fields of the seeded packings, all solved in one batch."""
+    import torch
+
+    cases = [channel_case(s, shape) for s in seeds]
+    geoms = [lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
+    c0 = cases[0]
+    solver = BatchSolver(geoms, c0.tau, c0.lam, c0.g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, steps, res = solver.run_until(tol, interval, max_steps, criterion="profile")
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError(f"training data did not converge: status {rc}, residual {res:.3e} after {steps} steps")
+    _, u = solver.moments()
+    nx, ny, nz = shape
+    per = nx * ny * nz
+    u = u.reshape(3, len(cases), per).permute(1, 0, 2).reshape(len(cases), 3, nz, ny, nx).contiguous()
+    sdf = torch.stack([lbm_sdf(g, SDF_TRUNC) for g in geoms])
+    return Dataset(sdf, u, cases, steps, secs)
+
+
+@dataclass
+class Training:
+    net: UNet
+    losses: list = field(default_factory=list)
+    seconds: float = 0.0
+    samples: int = 0
+
+
+def train(data: Dataset, epochs=30, lr=2e-3, batch=4, seed=0, lr_decay=0.1) -> Training:
+    """Adam on the mean squared error of the scaled fields (cosine decay of the
+    learning rate to lr * lr_decay)."""
+    import torch
+
+    n, _, nz, ny, nx = data.u.shape
+    batch = min(batch, n)
+    net = UNet(batch, nz, ny, nx, params=unet_init(seed))
+    tscale = 1.0 / velocity_scale(data.cases[0])
+    rng = np.random.default_rng(seed)
+    out = Training(net)
+    total = epochs * (n // batch)
+    it = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(epochs):
+        order = rng.permutation(n)
+        for b in range(n // batch):
+            idx = torch.as_tensor(order[b * batch:(b + 1) * batch], device=data.sdf.device)
+            sdf = data.sdf.index_select(0, idx).contiguous()
+            u = data.u.index_select(0, idx).contiguous()
+            net.forward(sdf)
+            out.losses.append(net.backward(u, tscale))
+            frac = it / max(1, total - 1)
+            net.adam_step(lr * (lr_decay + (1 - lr_decay) * 0.5 * (1 + np.cos(np.pi * frac))))
+            it += 1
+    torch.cuda.synchronize()
+    out.seconds = time.perf_counter() - t0
+    out.samples = it * batch
+    return out
+
+
+def predict(params, case: Channel, geom=None):
+    """Velocity field [3, nz, ny, nx] (lattice units) predicted for a case."""
+    import torch
+
+    geom = geom or lbm_geometry_from_spheres(*case.sphere_args())
+    net = UNet(1, case.nz, case.ny, case.nx, params=params)
+    sdf = lbm_sdf(geom, SDF_TRUNC).reshape(1, case.nz, case.ny, case.nx)
+    u = net.forward(sdf, out_scale=velocity_scale(case))
+    torch.cuda.synchronize()
+    return u[0]
+
+
+def time_to_steady(case: Channel, u0=None, tol=1e-8, interval=500, max_steps=2_000_000, geom=None) -> dict:
+    """Run one case to the plane-profile tolerance from rest (u0 None) or from
+    a predicted field; wall time includes the solver set-up."""
+    import torch
+
+    geom = geom or lbm_geometry_from_spheres(*case.sphere_args())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = Solver(geom, case.tau, case.lam, case.g, u0=u0)
+    rc, steps, res = s.run_until(tol, interval, max_steps, criterion="profile")
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"status": rc, "steps": steps, "residual": res, "seconds": secs,
+            "permeability": s.permeability(2, case.nz // 2 - 8)}
+
+
+def warm_vs_cold(params, seeds, shape=(64, 64, 128), tol=1e-8, interval=500) -> list:
+    """For each held-out seed: cold start, and warm start from the network
+    (inference time counted).  The permeability window is the porous layer
+    away from the interface."""
+    import torch
+
+    rows = []
+    for sd in seeds:
+        case = channel_case(sd, shape)
+        geom = lbm_geometry_from_spheres(*case.sphere_args())
+        cold = time_to_steady(case, None, tol, interval, geom=geom)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u0 = predict(params, case, geom).contiguous()
+        infer = time.perf_counter() - t0
+        warm = time_to_steady(case, u0, tol, interval, geom=geom)
+        warm["seconds"] += infer
+        warm["inference_s"] = infer
+        rows.append({"seed": sd, "porosity": case.porosity, "cold": cold, "warm": warm,
+                     "k_rel_diff": abs(warm["permeability"] / cold["permeability"] - 1.0)})
+    return rows

@@ -107,3 +107,24 @@ def velocity_field(shape, seed: int, amplitude: float = 1e-3) -> np.ndarray:
             ph = rng.uniform(0, 2 * np.pi)
             u[d] += rng.standard_normal() * np.cos(2 * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz) + ph)
     return (amplitude * u / max(1e-30, np.abs(u).max())).astype(np.float32)
+
+
+# The warm-start network's 3x3x3 layers (name, c_out, c_in) in parameter
+# order, as documented in include/unet.h; then the head [3][16] and bias [3].
+UNET_LAYERS = [("enc1a", 16, 16), ("enc1b", 16, 16), ("enc2a", 32, 16), ("enc2b", 32, 32),
+               ("enc3a", 64, 32), ("enc3b", 64, 64), ("botta", 128, 64), ("bottb", 128, 128),
+               ("dec3a", 64, 192), ("dec3b", 64, 64), ("dec2a", 32, 96), ("dec2b", 32, 32),
+               ("dec1a", 16, 48), ("dec1b", 16, 16)]
+
+
+def unet_init(seed: int) -> np.ndarray:
+    """Seeded He-uniform weights and zero biases as the flat fp32 parameter
+    vector of the warm-start network."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, co, ci in UNET_LAYERS:
+        bound = np.sqrt(6.0 / (27 * ci))
+        parts += [rng.uniform(-bound, bound, 27 * co * ci), np.zeros(co)]
+    bound = np.sqrt(6.0 / 16)
+    parts += [rng.uniform(-bound, bound, 3 * 16), np.zeros(3)]
+    return np.concatenate(parts).astype(np.float32)

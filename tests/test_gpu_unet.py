@@ -1,0 +1,159 @@
+"""The learned warm start on the GPU against its FP64 numpy oracle: signed
+distance, U-Net forward (oracle rounding activations and weights to bf16 the
+way the kernels store them), gradients of every layer, Adam, and a training
+smoke test."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import unet_oracle as U
+import paper_1507_06565_gb300 as L
+from paper_1507_06565_gb300 import workloads as W
+from paper_1507_06565_gb300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available()
+    build()
+    L.load_library()
+    return torch
+
+
+def flatten(p):
+    parts = []
+    for name, _, _ in U.layer_shapes():
+        parts += [p[name + ".w"].reshape(-1), p[name + ".b"]]
+    parts += [p["head.w"].reshape(-1), p["head.b"]]
+    return np.concatenate(parts)
+
+
+def unflatten(v):
+    out, off = {}, 0
+    for name, co, ci in U.layer_shapes():
+        n = 27 * co * ci
+        out[name + ".w"] = v[off:off + n].reshape(27, co, ci)
+        off += n
+        out[name + ".b"] = v[off:off + co]
+        off += co
+    out["head.w"] = v[off:off + 48].reshape(3, 16)
+    out["head.b"] = v[off + 48:off + 51]
+    assert off + 51 == v.size
+    return out
+
+
+@pytest.mark.parametrize("case", [W.small_cases()[0], W.small_cases()[2]], ids=lambda c: c.name)
+def test_sdf_matches_oracle(torch_cuda, case):
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+    got = L.lbm_sdf(geom, 6.0).cpu().numpy()
+    want = U.sdf(case.nx, case.ny, case.nz, case.periodic_z, geom.spheres(), 6.0)
+    assert np.max(np.abs(got - want)) < 2e-6
+    assert np.array_equal(got < 0, want < 0) or np.mean((got < 0) != (want < 0)) < 1e-4
+
+
+def _setup(torch, shape=(16, 16, 16), seed=5):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    p = U.init_params(seed)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = 0.05 * rng.standard_normal(p[k].shape)
+    case = W.Channel("unet box", nx, ny, nz, 1.0, nz / 2, 2.0, 3.0, 0.7, True, seed)
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+    sdf = U.sdf(nx, ny, nz, False, geom.spheres(), 4.0)
+    net = L.UNet(1, nz, ny, nx, params=flatten(p).astype(np.float32))
+    sdf_t = torch.from_numpy(sdf.astype(np.float32)).cuda().reshape(1, nz, ny, nx)
+    return p, sdf, net, sdf_t
+
+
+def test_unet_forward_matches_oracle(torch_cuda):
+    p, sdf, net, sdf_t = _setup(torch_cuda)
+    out = net.forward(sdf_t).cpu().numpy()[0]
+    p32 = unflatten(flatten(p).astype(np.float32).astype(np.float64))
+    want = U.UNet(p32, bf16_emulation=True).forward(U.input_channels(sdf))
+    err = np.abs(out - want)
+    scale = np.max(np.abs(want))
+    assert np.sqrt(np.mean(err ** 2)) <= 2e-3 * scale
+    assert np.max(err) <= 2e-2 * scale
+
+
+def test_unet_backward_matches_oracle(torch_cuda):
+    """Gradients against the oracle that rounds what the kernels store to
+    bf16: the remaining differences are the rounding of values the two sides
+    compute in a different order (relative 2% at most on 32^3, measured)."""
+    torch = torch_cuda
+    p, sdf, net, sdf_t = _setup(torch, shape=(32, 32, 32))
+    rng = np.random.default_rng(9)
+    target = rng.standard_normal((3,) + sdf.shape) * 0.5
+    net.forward(sdf_t)
+    loss = net.backward(torch.from_numpy(target.astype(np.float32)).cuda().reshape(1, 3, *sdf.shape))
+    g = unflatten(net.grads().cpu().numpy().astype(np.float64))
+    p32 = unflatten(flatten(p).astype(np.float32).astype(np.float64))
+    ref = U.UNet(p32, bf16_emulation=True)
+    out = ref.forward(U.input_channels(sdf))
+    assert abs(loss / ref.loss(out, target) - 1) < 1e-3
+    gw = ref.backward(target)
+    for name, _, _ in U.layer_shapes():
+        for suffix in (".w", ".b"):
+            a, b = g[name + suffix].reshape(-1), gw[name + suffix].reshape(-1)
+            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+            cos = np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b))
+            assert rel < 3e-2 and cos > 0.999, (name + suffix, rel, cos)
+    for k in ("head.w", "head.b"):
+        assert np.linalg.norm(g[k] - gw[k]) / np.linalg.norm(gw[k]) < 1e-2
+
+
+def test_adam_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    p, sdf, net, sdf_t = _setup(torch)
+    target = np.ones((3,) + sdf.shape) * 0.1
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda().reshape(1, 3, *sdf.shape)
+    params = flatten(p).astype(np.float32).astype(np.float64)
+    state = {}
+    for _ in range(3):
+        net.forward(sdf_t)
+        net.backward(tgt)
+        grads = net.grads().cpu().numpy().astype(np.float64)
+        net.adam_step(lr=1e-3)
+        pd = {"all": params}
+        U.adam(pd, {"all": grads}, state, lr=1e-3)
+        params = pd["all"]
+    got = net.params().cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - params)) < 1e-6
+
+
+def test_training_reduces_loss(torch_cuda):
+    torch = torch_cuda
+    p, sdf, net, sdf_t = _setup(torch, shape=(16, 32, 32))
+    nz = sdf.shape[0]
+    z = np.linspace(0, 1, nz)[:, None, None]
+    prof = (4 * z * (1 - z)) * (sdf > 0)
+    target = np.stack([prof, 0 * prof, 0 * prof]) * 0.3
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda().reshape(1, 3, *sdf.shape)
+    losses = []
+    for _ in range(60):
+        net.forward(sdf_t)
+        losses.append(net.backward(tgt))
+        net.adam_step(lr=2e-3)
+    assert losses[-1] < 0.3 * losses[0], losses[::10]
+
+
+def test_backward_at_training_size(torch_cuda):
+    """Batch 4 of 128 x 64 x 64 fields (2.1 M voxels): the weight-gradient
+    grid then has 110,592 (chunk, tap) blocks, more than a grid's y or z
+    extent allows; the pass must run and give finite gradients."""
+    torch = torch_cuda
+    n, nz, ny, nx = 4, 128, 64, 64
+    net = L.UNet(n, nz, ny, nx, params=W.unet_init(0))
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    sdf = torch.rand((n, nz, ny, nx), device="cuda", generator=gen) * 2 - 1
+    tgt = torch.rand((n, 3, nz, ny, nx), device="cuda", generator=gen) * 0.1
+    net.forward(sdf)
+    loss = net.backward(tgt)
+    gr = net.grads()
+    assert np.isfinite(loss) and loss > 0
+    assert bool(torch.isfinite(gr).all()) and float(gr.abs().max()) > 0
