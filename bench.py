@@ -34,6 +34,10 @@ FALLBACK_HBM_GBS = 6800.0
 METRIC = "fluid MLUPS (D3Q19 TRT + CLI stream-collide; HBM roofline fraction in 'roofline')"
 WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlapping r=8 spheres, "
             "porosity sweep {0.4,0.6,0.8,0.9} (one solver each); one step = one time step of all four")
+# measured DRAM read + write bytes per fluid cell of one launch (FP32 storage,
+# neighbour table): ncu on the default command, full-grid launches of all four
+# solvers (see profiles/step_kernels_channel_256x256x512_dram.txt)
+MEASURED_DRAM_B_PER_FLUP = {"even": 155.2, "odd": 223.5}
 # bounded samples of the workload for the CPU oracle: same sphere radius,
 # porosity and channel structure at a reduced box
 SAMPLE = W.Channel("W2-shaped sample 128x128x256 r=8 phi=0.6", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, 0.6, True, 2060)
@@ -148,9 +152,17 @@ def workload_name(args):
     if args.workload == "channel":
         return WORKLOAD
     if args.workload == "channel-half":
-        return WORKLOAD.replace("256x256x512", "128x128x256")
+        return (WORKLOAD.replace("256x256x512", "128x128x256").replace("z=0/511", "z=0/255")
+                .replace("z<256", "z<128"))
     return (f"{args.cubes} periodic REV cubes (edge U[48,160], r U[3,10], porosity U[0.35,0.95], seeds 4000+i) "
             "as one batch: one launch per step for all cubes")
+
+
+def odd_flags(args) -> int:
+    import paper_1507_06565_gb300 as L
+
+    return {"auto": 0, "table": L.LBM_FLAG_NEIGHBOUR_TABLE,
+            "rows": L.LBM_FLAG_ROW_NEIGHBOURS}[getattr(args, "odd", "auto")]
 
 
 def run_converge(args):
@@ -167,13 +179,13 @@ def run_converge(args):
     if args.workload == "rev":
         cases = [W.W4_cube(i) for i in range(args.cubes)]
         geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
-        solvers = [L.BatchSolver(geoms, cases[0].tau, cases[0].lam, cases[0].g, args.storage)]
+        solvers = [L.BatchSolver(geoms, cases[0].tau, cases[0].lam, cases[0].g, args.storage, flags=odd_flags(args))]
     else:
         cases = [W.W2(phi) for phi in W.W2_POROSITIES] if args.workload == "channel" else [
             W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True, W.W2(phi).seed)
             for phi in W.W2_POROSITIES]
         geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
-        solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage) for g, c in zip(geoms, cases)]
+        solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage, flags=odd_flags(args)) for g, c in zip(geoms, cases)]
     out = []
     total_s = 0.0
     for s, c in zip(solvers, cases):
@@ -272,9 +284,9 @@ def run_ours(args, world, rank, local):
     geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
     c0 = cases[0]
     if args.workload == "rev":
-        solvers = [L.BatchSolver(geoms, c0.tau, c0.lam, c0.g, args.storage)]
+        solvers = [L.BatchSolver(geoms, c0.tau, c0.lam, c0.g, args.storage, flags=odd_flags(args))]
     else:
-        solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage) for g, c in zip(geoms, cases)]
+        solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage, flags=odd_flags(args)) for g, c in zip(geoms, cases)]
     nfs = [s.info()["n_fluid"] for s in solvers]
     nf_total = sum(nfs)
     lib = L.load_library()
@@ -334,6 +346,13 @@ def run_ours(args, world, rank, local):
             parity[name] = float((bytes_per_launch[None, :] / (sel * 1e-3)).mean() / 1e9)
     peak, peak_kind = _peak_hbm()
     value = nf_total * args.steps * world / (ms * 1e-3) / 1e6
+    # DRAM bytes per fluid cell and launch of the step kernels as they stand,
+    # from one ncu capture of this command (dram__bytes_read.sum +
+    # dram__bytes_write.sum, profiles/step_kernels_channel_256x256x512_dram.txt):
+    # only for the configuration it was taken on
+    traffic = None
+    if args.workload == "channel" and args.storage == "f32" and args.odd == "auto":
+        traffic = float(np.mean(nfs)) * 0.5 * (MEASURED_DRAM_B_PER_FLUP["even"] + MEASURED_DRAM_B_PER_FLUP["odd"])
 
     # end to end through the public API with host buffers: lbm_init from the
     # host geometry (mask and sphere bins copied host->device), E2E_STEPS
@@ -346,9 +365,9 @@ def run_ours(args, world, rank, local):
     groups = [geoms] if args.workload == "rev" else [[g] for g in geoms]
     for grp in groups:
         if args.workload == "rev":
-            s2 = L.BatchSolver(grp, c0.tau, c0.lam, c0.g, args.storage)
+            s2 = L.BatchSolver(grp, c0.tau, c0.lam, c0.g, args.storage, flags=odd_flags(args))
         else:
-            s2 = L.Solver(grp[0], c0.tau, c0.lam, c0.g, args.storage)
+            s2 = L.Solver(grp[0], c0.tau, c0.lam, c0.g, args.storage, flags=odd_flags(args))
         s2.step(e2e_steps)
         pa = s2.plane_average()
         h2d += sum(g.mask().nbytes for g in grp)
@@ -362,12 +381,12 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage,
+        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage, "odd_neighbours": args.odd,
                    "schedule": schedules,
                    "l2": "inputs larger than L2 (4.1-5.7 GB of populations and indices per solver)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_step_even/k_step_odd (fused AA stream-collide + CLI)",
                      "bytes_per_flup": bytes_per_flup, "peak_kind": peak_kind, "by_parity": parity},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / e2e_steps,
@@ -392,6 +411,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--odd", choices=["auto", "table", "rows"], default="auto",
+                    help="neighbour indices of the odd step (library default, int32 table, row bitmasks)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
     ap.add_argument("--workload", choices=["channel", "channel-half", "rev", "surrogate"], default="channel",

@@ -98,9 +98,9 @@ typedef struct {
  * differ only in FP32 rounding.  LBM_FLAG_NEIGHBOUR_TABLE reads the 18 neighbour indices of a cell
  * from the stored table (72 bytes per cell and odd step);
  * LBM_FLAG_ROW_NEIGHBOURS computes them from per-row fluid bitmasks (about
- * 4 bytes per cell).  Neither: the library picks the table for FP32 storage
- * and the bitmasks for 16-bit storage.  The table is used whenever ny*nz does
- * not fit beside x in 32 bits. */
+ * 4 bytes per cell, but two dependent loads before the gathers).  Neither:
+ * the table, which measured faster for every storage type.  The table is also
+ * used whenever ny*nz does not fit beside x in 32 bits. */
 #define LBM_FLAG_NEIGHBOUR_TABLE 1
 #define LBM_FLAG_ROW_NEIGHBOURS 2
 /* Scheduling switches.  By default lbm_step times a few grid sizes for each

@@ -216,7 +216,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->n_words = (s->box.nx + 31) / 32;
     s->x_bits = x_bits_for(s->box.nx);
     {
-        bool rows = params->storage != LBM_F32;   // auto: see LBM_FLAG_* in lbm.h
+        bool rows = false;   // auto: the table (see LBM_FLAG_* in lbm.h)
         if (params->flags & LBM_FLAG_NEIGHBOUR_TABLE) rows = false;
         if (params->flags & LBM_FLAG_ROW_NEIGHBOURS) rows = true;
         s->odd_rows = rows && single && rows_packable(s->box);

@@ -80,6 +80,13 @@ __device__ __forceinline__ uint32_t first_link(const uint32_t *__restrict__ warp
     return warp_off[i >> 5] + incl - cnt;
 }
 
+// CLI coefficient of direction k (0 unless k is a link of mask m): the links of
+// a cell are stored in increasing k from its first link `off`.
+__device__ __forceinline__ float link_coef(const float *__restrict__ link_a, uint32_t off, uint32_t m, int k)
+{
+    return ((m >> k) & 1u) ? link_a[off + __popc(m & ((1u << k) - 1u))] : 0.0f;
+}
+
 // CLI coefficients a[k] of the links in m (0 elsewhere).
 __device__ __forceinline__ void load_links(float a[kQ], uint32_t m, const float *__restrict__ link_a, uint32_t off)
 {

@@ -20,10 +20,12 @@ namespace {
 
 // Resident blocks per SM requested from the register allocator (256 threads
 // each).  Measured on GB300 over the 256x256x512 channel sweep: the even step
-// reaches 91% of the copy bandwidth at 5 blocks (48 registers, no spills); the
-// odd step is best at 4 (64 registers); more blocks make the odd step spill.
-constexpr int kEvenBlocksPerSM = 5;
-constexpr int kOddBlocksPerSM = 4;
+// (no shared memory) reaches 93% of the copy bandwidth at 6 blocks (40
+// registers, no spills; 7 spills); the odd step is best at 5 (48 registers,
+// 180 KB of staging per SM): at 6 its staging leaves too little L1 for the
+// neighbour gathers, which hit L1 about a third of the time.
+constexpr int kEvenBlocksPerSM = 6;
+constexpr int kOddBlocksPerSM = 5;
 constexpr int kGraphSteps = 32;     // steps per CUDA-graph replay (even)
 constexpr int kTuneReps = 3;        // timed launches per candidate grid
 
@@ -58,15 +60,13 @@ __device__ __forceinline__ float part_shift_of(const StepArgs<T> &p, int32_t i)
     return __ldg(p.part_shift + lo);
 }
 
-// Per-thread staging in shared memory: the CLI coefficients (and, for the odd
-// step, the neighbour indices) of a thread are written and read by that thread
-// only, so no barrier is needed.  Keeping them out of registers across the
-// collision lowers register pressure and raises the number of resident warps,
-// which is what hides the memory latency of these kernels.
+// Even step: the cell's own 19 slots.  The CLI coefficients of its links are
+// read where they are used, before and after the collision; the second read
+// hits L1.  Holding no staging buffer keeps shared memory free for L1 and the
+// register count at 40, so six blocks fit on an SM.
 template <typename T>
-__device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i, float (*a_s)[kBlock])
+__device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 {
-    const int t = threadIdx.x;
     const bool live = i < p.n_fluid;
     const uint32_t m = live ? p.lmask[i] : 0u;
     const uint32_t off = first_link(p.warp_off, i, m);
@@ -75,16 +75,25 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i, float
     float h[kQ];
     gather_even(h, p.pdf, n_pad, i);
     if (m) {
-        stage_links(a_s, t, m, p.link_a, off);
-        cli_incoming_s(h, a_s, t);
+#pragma unroll
+        for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(link_coef(p.link_a, off, m, k), h[k], h[opp(k)]);
     }
     if (p.shift_on) apply_shift(h, part_shift_of(p, i));
     collide(h, p.c);
-    if (m) cli_outgoing_s(h, a_s, t);
+    if (m) {
+#pragma unroll
+        for (int k = 1; k < kQ; ++k) h[k] = fmaf(-link_coef(p.link_a, off, m, k), h[opp(k)], h[k]);
+    }
 #pragma unroll
     for (int k = 0; k < kQ; ++k) st(p.pdf + opp(k) * n_pad + i, h[k]);
 }
 
+// Odd step: per-thread staging in shared memory.  The CLI coefficients and
+// the neighbour indices of a thread are written and read by that thread only,
+// so no barrier is needed.  Keeping them out of registers across the
+// collision lowers register pressure and raises the number of resident warps,
+// which is what hides the memory latency of the two dependent loads (indices,
+// then populations).
 // ROWS: neighbour indices from the row bitmasks; otherwise from the table.
 template <typename T, bool ROWS>
 __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock],
@@ -126,8 +135,7 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
 template <typename T, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
 {
-    __shared__ float a_s[kQ - 1][kBlock];
-    for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) even_cell(p, tile * kBlock + threadIdx.x, a_s);
+    for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) even_cell(p, tile * kBlock + threadIdx.x);
 }
 
 template <typename T, bool ROWS, int MINB>
