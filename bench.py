@@ -154,6 +154,9 @@ def workload_name(args):
     if args.workload == "channel-half":
         return (WORKLOAD.replace("256x256x512", "128x128x256").replace("z=0/511", "z=0/255")
                 .replace("z<256", "z<128"))
+    if args.workload == "large":
+        return ("512x512x1024 channel, walls z=0/1023, porous layer z<512 of overlapping r=8 spheres, porosity 0.6 "
+                "(seed 3060); one step = one time step of the box")
     return (f"{args.cubes} periodic REV cubes (edge U[48,160], r U[3,10], porosity U[0.35,0.95], seeds 4000+i) "
             "as one batch: one launch per step for all cubes")
 
@@ -279,6 +282,8 @@ def run_ours(args, world, rank, local):
     elif args.workload == "channel-half":   # the same channel at half the size, for profiler captures
         cases = [W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True,
                            W.W2(phi).seed) for phi in W.W2_POROSITIES]
+    elif args.workload == "large":   # one 512x512x1024 channel (W2's structure, porosity 0.6)
+        cases = [W.W3_LARGE]
     else:   # rev: the periodic REV cubes as one batch
         cases = [W.W4_cube(i) for i in range(args.cubes)]
     geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
@@ -383,7 +388,8 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage, "odd_neighbours": args.odd,
                    "schedule": schedules,
-                   "l2": "inputs larger than L2 (4.1-5.7 GB of populations and indices per solver)",
+                   "l2": "inputs larger than L2 ({:.1f}-{:.1f} GB of populations and indices per solver)".format(
+                       *(n * (19 * (4 if args.storage == "f32" else 2) + 76) / 1e9 for n in (min(nfs), max(nfs)))),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -415,9 +421,10 @@ def main():
                     help="neighbour indices of the odd step (library default, int32 table, row bitmasks)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
-    ap.add_argument("--workload", choices=["channel", "channel-half", "rev", "surrogate"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "rev", "surrogate"], default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
-                         "profiling; rev: the batched REV cubes")
+                         "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
+                         "warm versus cold start")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
