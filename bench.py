@@ -51,6 +51,26 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """The largest of `value` over all ranks (the slowest rank's time); the
+    value itself without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ms: float, world: int) -> float:
+    """Millions of units per second over the whole job: every rank processes
+    the same units (replicas, weak scaling), the job takes the slowest rank's
+    time."""
+    return units_per_rank * world / (ms * 1e-3) / 1e6
+
+
 def _peak_hbm():
     try:
         with open(PEAKS_FILE) as fh:
@@ -332,11 +352,7 @@ def run_ours(args, world, rank, local):
     t1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1))
     durs = np.array([a.elapsed_time(b) for a, b in zip(*ev)]).reshape(args.steps, len(solvers))
     first_parity = args.warmup & 1   # parity of the first timed step
     # per-launch algorithmic bytes: 19 loads + 19 stores of the stored type per fluid cell
@@ -350,7 +366,7 @@ def run_ours(args, world, rank, local):
             name = "even" if (first_parity + off) % 2 == 0 else "odd"
             parity[name] = float((bytes_per_launch[None, :] / (sel * 1e-3)).mean() / 1e9)
     peak, peak_kind = _peak_hbm()
-    value = nf_total * args.steps * world / (ms * 1e-3) / 1e6
+    value = whole_job_rate(nf_total * args.steps, ms, world)
     # DRAM bytes per fluid cell and launch of the step kernels as they stand,
     # from one ncu capture of this command (dram__bytes_read.sum +
     # dram__bytes_write.sum, profiles/step_kernels_channel_256x256x512_dram.txt):

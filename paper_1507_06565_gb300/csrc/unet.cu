@@ -12,15 +12,17 @@
 //
 // Numerics: activations, activation gradients and the working copies of the
 // weights are bf16 (layout [voxel][channel]); every contraction accumulates in
-// fp32 on the tensor cores (mma.sync m16n8k16, bf16 inputs); master weights,
-// weight gradients and the Adam moments are fp32.  The 3x3x3 convolution is an
-// implicit GEMM: M = voxels, N = output channels, K = 27 taps x input
-// channels; its backward with respect to the input is the same kernel with
+// fp32 on the tensor cores; master weights, weight gradients and the Adam
+// moments are fp32.  The 3x3x3 convolution is an implicit GEMM (M = voxels,
+// N = output channels, K = 27 taps x input channels) on tcgen05 with a TMEM
+// accumulator; its backward with respect to the input is the same kernel with
 // the weights flipped in the taps and transposed in the channels (the adjoint
-// of a circular/zero-padded convolution); the weight gradient contracts over
-// voxels with the tensor cores and adds block partials atomically.
+// of a circular/zero-padded convolution).  The weight gradient contracts over
+// voxels with warp-level MMAs (mma.sync m16n8k16) and adds block partials
+// atomically.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -97,78 +99,246 @@ struct ConvArgs {
     Dims g;
 };
 
-constexpr int kConvBM = 64;        // voxels per block (4 warps x 16 rows)
 constexpr int kPadK = 24;          // smem row length in bf16 (16 + 8 padding: conflict-free fragments)
 
-template <int BN>
-__global__ void __launch_bounds__(128) k_conv3(ConvArgs a)
+// ---------------------------------------------------------------------------
+// The convolution on the 5th-generation tensor cores (tcgen05): one CTA
+// of 128 threads computes a tile of 128 voxels x all N = co output channels
+// into a TMEM accumulator (128 lanes x N fp32 columns).  K runs over the 27
+// taps and chunks of KC input channels; each K step stages, for TP taps, the
+// gathered A tile (128 voxels x KC channels of the tap's neighbours) and the
+// B tile (N x KC weights) in shared memory with cp.async (zero-fill for voxels past the
+// end and for the zero padding in z), in 2-4 stages (two as launched), and one thread issues
+// TP*KC/16 MMAs (M=128, K=16) and commits them to the stage's mbarrier, which
+// frees the stage.  Operands are K-major without swizzle, in 8x8 core
+// matrices of 16-byte rows: core (row/8, k/8) at (row/8)*SBO + (k/8)*128 with
+// SBO = KC/8 * 128.  The epilogue reads the accumulator with tcgen05.ld
+// (warp w owns lanes 32w..32w+31, i.e. its 32 voxels), adds the bias, applies
+// the ReLU and stores bf16.  Waits on mbarriers are bounded; a wait that runs
+// out sets *a.status and the CTA still frees its TMEM.
+// ---------------------------------------------------------------------------
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor (sm_100 family): start, leading (K-direction
+// core) offset, stride (8-row group) offset, all >> 4; version bit 46; no swizzle
+__device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    __shared__ __align__(16) bf16 As[kConvBM][kPadK];
-    __shared__ __align__(16) bf16 Bs[BN][kPadK];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-    const int64_t m0 = (int64_t)blockIdx.x * kConvBM;
-    const int n0 = blockIdx.y * BN;
-    const int ci = a.ci0 + a.ci1, co = a.co0 + a.co1;
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N/8 at bit 17, M/16 at bit 24
+__device__ __forceinline__ uint32_t idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool try_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false (and *status set) if the phase did not complete
+__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity, int *status)
+{
+    for (int it = 0; it < (1 << 24); ++it)
+        if (try_wait(mbar, parity)) return true;
+    atomicExch(status, 1);
+    return false;
+}
+
+}  // namespace tc
+
+constexpr int kTcM = 128;
+constexpr int kTcMaxStages = 4;
+
+__global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, int ncols, int stages, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[kTcMaxStages];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ci = a.ci0 + a.ci1, n = a.co0 + a.co1;
     const int64_t V = a.g.voxels();
-    float acc[BN / 8][4];
-#pragma unroll
-    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-    // the A row this thread stages (two threads per row, 8 channels each)
-    const int arow = tid >> 1, ahalf = tid & 1;
-    const int64_t av = m0 + arow;
-    for (int t = 0; t < kTaps; ++t) {
-        const int64_t nb = av < V ? tap_neighbour(a.g, av, t) : -1;
-        for (int c0 = 0; c0 < ci; c0 += 16) {
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (nb >= 0) {
-                const bf16 *src = c0 < a.ci0 ? a.in0 + nb * a.ci0 + c0 : a.in1 + nb * a.ci1 + (c0 - a.ci0);
-                val = *reinterpret_cast<const uint4 *>(src + ahalf * 8);
+    const int64_t m0 = (int64_t)blockIdx.x * kTcM;
+    // a step gathers tp taps x kc channels: tp A sub-tiles, then tp B sub-tiles
+    const uint32_t a_bytes = (uint32_t)kTcM * kc * 2, b_bytes = (uint32_t)n * kc * 2;
+    const uint32_t stage_bytes = (uint32_t)tp * (a_bytes + b_bytes), sbo = (uint32_t)(kc / 8) * 128u;
+    const uint32_t base = tc::smem_u32(smem);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         tc::smem_u32(&tmem_base)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0)
+        for (int q = 0; q < stages; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::smem_u32(&mbar[q])));
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    // this thread's voxel (row tid of the tile) and its coordinates
+    const int64_t v = m0 + tid;
+    const bool vin = v < V;
+    int x = 0, y = 0, z = 0;
+    int64_t nn = 0;
+    if (vin) {
+        x = (int)(v % a.g.w);
+        int64_t r = v / a.g.w;
+        y = (int)(r % a.g.h);
+        r /= a.g.h;
+        z = (int)(r % a.g.d);
+        nn = r / a.g.d;
+    }
+    const int chunks = ci / kc, iters = (kTaps / tp) * chunks;
+    const uint32_t id = tc::idesc(kTcM, n);
+    bool ok = true;
+
+    auto fill = [&](int it, int s) {
+        const int tg = it / chunks, c0 = (it % chunks) * kc;
+        const uint32_t row_off = (uint32_t)(tid >> 3) * sbo + (uint32_t)(tid & 7) * 16u;
+        for (int q = 0; q < tp; ++q) {
+            const int t = tg * tp + q;
+            const uint32_t sa = base + (uint32_t)s * stage_bytes + (uint32_t)q * a_bytes;
+            const uint32_t sb = base + (uint32_t)s * stage_bytes + (uint32_t)tp * a_bytes + (uint32_t)q * b_bytes;
+            // A: row tid, kc/8 chunks of 8 channels of the tap's neighbour
+            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+            const int zz = z + dz;
+            const bool valid = vin && zz >= 0 && zz < a.g.d;
+            int yy = y + dy, xx = x + dx;
+            yy = yy < 0 ? yy + a.g.h : (yy >= a.g.h ? yy - a.g.h : yy);
+            xx = xx < 0 ? xx + a.g.w : (xx >= a.g.w ? xx - a.g.w : xx);
+            const int64_t nb = valid ? ((nn * a.g.d + zz) * a.g.h + yy) * a.g.w + xx : 0;
+            for (int j = 0; j < kc / 8; ++j) {
+                const int c = c0 + 8 * j;
+                const bf16 *src = c < a.ci0 ? a.in0 + nb * a.ci0 + c : a.in1 + nb * a.ci1 + (c - a.ci0);
+                tc::cp16(sa + row_off + (uint32_t)j * 128u, valid ? (const void *)src : (const void *)a.in0, valid);
             }
-            *reinterpret_cast<uint4 *>(&As[arow][ahalf * 8]) = val;
-            if (tid < 2 * BN) {
-                const int brow = tid >> 1, bhalf = tid & 1;
-                uint4 wv = make_uint4(0u, 0u, 0u, 0u);
-                if (n0 + brow < co)
-                    wv = *reinterpret_cast<const uint4 *>(a.w + ((int64_t)t * co + n0 + brow) * ci + c0 + bhalf * 8);
-                *reinterpret_cast<uint4 *>(&Bs[brow][bhalf * 8]) = wv;
+            // B: n rows x kc/8 chunks of the tap's weights
+            for (int e = tid; e < n * (kc / 8); e += 128) {
+                const int r = e / (kc / 8), j = e % (kc / 8);
+                const bf16 *src = a.w + ((int64_t)t * n + r) * ci + c0 + 8 * j;
+                tc::cp16(sb + (uint32_t)(r >> 3) * sbo + (uint32_t)j * 128u + (uint32_t)(r & 7) * 16u, src, true);
             }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    auto issue = [&](int it, int s) {
+        for (int q = 0; q < tp; ++q) {
+            const uint32_t sa = base + (uint32_t)s * stage_bytes + (uint32_t)q * a_bytes;
+            const uint32_t sb = base + (uint32_t)s * stage_bytes + (uint32_t)tp * a_bytes + (uint32_t)q * b_bytes;
+            for (int j = 0; j < kc / 16; ++j) {
+                const uint64_t ad = tc::desc(sa + (uint32_t)j * 256u, 128u, sbo);
+                const uint64_t bd = tc::desc(sb + (uint32_t)j * 256u, 128u, sbo);
+                const uint32_t acc = (it > 0 || q > 0 || j > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(id), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         tc::smem_u32(&mbar[s]))
+                     : "memory");
+    };
+
+    // step it: (1) wait until the MMAs of step it - stages, which read stage
+    // it % stages, are done; (2) gather step it into that stage; (3) once the
+    // gather of step it - (stages - 1) has landed, issue its MMAs.  A gather
+    // thus has stages - 1 steps to arrive and an MMA one step to finish.
+    const int lag = stages - 1;
+    for (int it = 0; it < iters; ++it) {
+        const int s = it % stages;
+        if (it >= stages) {
+            // thread 0 waits; the barrier hands its verdict to the whole CTA
+            int w = 1;
+            if (tid == 0) w = tc::wait(tc::smem_u32(&mbar[s]), (uint32_t)((it / stages - 1) & 1), status) ? 1 : 0;
+            ok = __syncthreads_and(w) != 0;
+            if (!ok) break;
+        }
+        fill(it, s);
+        if (it >= lag) {
+            if (lag == 3) asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+            else if (lag == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+            else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncthreads();
-            uint32_t af[4];
-            const int r = warp * 16 + g;
-            af[0] = *reinterpret_cast<const uint32_t *>(&As[r][2 * t4]);
-            af[1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * t4]);
-            af[2] = *reinterpret_cast<const uint32_t *>(&As[r][2 * t4 + 8]);
-            af[3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * t4 + 8]);
-#pragma unroll
-            for (int j = 0; j < BN / 8; ++j) {
-                uint32_t bfr[2];
-                bfr[0] = *reinterpret_cast<const uint32_t *>(&Bs[8 * j + g][2 * t4]);
-                bfr[1] = *reinterpret_cast<const uint32_t *>(&Bs[8 * j + g][2 * t4 + 8]);
-                mma_bf16(acc[j], af, bfr);
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                issue(it - lag, (it - lag) % stages);
             }
-            __syncthreads();
         }
     }
-    // epilogue: bias, ReLU, bf16 pairs to the output channel range
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (ok) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        int w = 1;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int j = iters - lag; j < iters; ++j) issue(j, j % stages);
+            // the last commit tracks every MMA issued before it
+            const int l = iters - 1;
+            w = tc::wait(tc::smem_u32(&mbar[l % stages]), (uint32_t)((l / stages) & 1), status) ? 1 : 0;
+        }
+        ok = __syncthreads_and(w) != 0;
+    } else {
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        // epilogue: warp w reads its 32 lanes (voxels), 16 columns at a time
+        const int64_t row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < n; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < V) {
+                uint32_t packed[8];
 #pragma unroll
-    for (int j = 0; j < BN / 8; ++j) {
-        const int c = n0 + 8 * j + 2 * t4;
-        if (c >= co) continue;
-        const float b0 = a.bias ? a.bias[c] : 0.0f, b1 = a.bias ? a.bias[c + 1] : 0.0f;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int64_t v = m0 + warp * 16 + g + 8 * half;
-            if (v >= V) continue;
-            float y0 = acc[j][2 * half] + b0, y1 = acc[j][2 * half + 1] + b1;
-            if (a.relu) {
-                y0 = fmaxf(y0, 0.0f);
-                y1 = fmaxf(y1, 0.0f);
+                for (int j = 0; j < 8; ++j) {
+                    const int c = c0 + 2 * j;
+                    float y0 = __uint_as_float(r[2 * j]) + (a.bias ? a.bias[c] : 0.0f);
+                    float y1 = __uint_as_float(r[2 * j + 1]) + (a.bias ? a.bias[c + 1] : 0.0f);
+                    if (a.relu) {
+                        y0 = fmaxf(y0, 0.0f);
+                        y1 = fmaxf(y1, 0.0f);
+                    }
+                    const __nv_bfloat162 pr = __floats2bfloat162_rn(y0, y1);
+                    packed[j] = *reinterpret_cast<const uint32_t *>(&pr);
+                }
+                // 16 channels lie in one of the two outputs (co0 is a multiple of 16)
+                bf16 *dst = c0 < a.co0 ? a.out0 + row * a.co0 + c0 : a.out1 + row * a.co1 + (c0 - a.co0);
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                d4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                d4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
             }
-            const __nv_bfloat162 pr = __floats2bfloat162_rn(y0, y1);
-            bf16 *dst = c < a.co0 ? a.out0 + v * a.co0 + c : a.out1 + v * a.co1 + (c - a.co0);
-            *reinterpret_cast<__nv_bfloat162 *>(dst) = pr;
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
 }
 
 // ---------------------------------------------------------------------------
@@ -354,39 +524,56 @@ __global__ void k_head(const bf16 *__restrict__ x, const float *__restrict__ w, 
 // loss and head backward: dout = 2 (out - tscale * target) / (3 V);
 // dx[v][c] = sum_o W[o][c] dout[v][o]; head weight/bias gradients and the
 // loss (sum of squares) accumulate per block.
-__global__ void k_head_back(const bf16 *__restrict__ x, const float *__restrict__ w, const float *__restrict__ out_norm,
-                            const float *__restrict__ target, float tscale, Dims g, bf16 *__restrict__ dx,
-                            float *__restrict__ dw, float *__restrict__ db, double *__restrict__ loss)
+__global__ void __launch_bounds__(256, 2) k_head_back(const bf16 *__restrict__ x, const float *__restrict__ w,
+                                                   const float *__restrict__ out_norm, const float *__restrict__ target,
+                                                   float tscale, Dims g, bf16 *__restrict__ dx, float *__restrict__ dw,
+                                                   float *__restrict__ db, double *__restrict__ loss)
 {
+    // per-thread partial sums over a grid-stride loop, then warp shuffles,
+    // then one shared-memory add per warp and one global add per block
     __shared__ float sw[kOut * 16 + kOut];
+    __shared__ float wb[kOut * 16];   // the head weights as the forward used them (bf16)
     __shared__ double sl;
     if (threadIdx.x < kOut * 16 + kOut) sw[threadIdx.x] = 0.0f;
+    if (threadIdx.x < kOut * 16) wb[threadIdx.x] = __bfloat162float(__float2bfloat16_rn(w[threadIdx.x]));
     if (threadIdx.x == 0) sl = 0.0;
     __syncthreads();
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t V = g.voxels();
-    if (v < V) {
-        const int64_t per = (int64_t)g.d * g.h * g.w;
+    float pw[kOut * 16 + kOut];
+#pragma unroll
+    for (int e = 0; e < kOut * 16 + kOut; ++e) pw[e] = 0.0f;
+    double l = 0.0;
+    const int64_t V = g.voxels(), per = (int64_t)g.d * g.h * g.w;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t n = v / per, cell = v % per;
         float d[kOut];
-        double l = 0.0;
+#pragma unroll
         for (int o = 0; o < kOut; ++o) {
             const float diff = out_norm[v * kOut + o] - tscale * target[(n * kOut + o) * per + cell];
             l += (double)diff * diff;
             d[o] = 2.0f * diff / (float)(kOut * V);
+            pw[kOut * 16 + o] += d[o];
         }
-        atomicAdd(&sl, l);
+#pragma unroll
         for (int c = 0; c < 16; ++c) {
             const float xc = __bfloat162float(x[v * 16 + c]);
-            float s = 0.0f;
+            float sacc = 0.0f;
+#pragma unroll
             for (int o = 0; o < kOut; ++o) {
-                s += __bfloat162float(__float2bfloat16_rn(w[o * 16 + c])) * d[o];
-                atomicAdd(&sw[o * 16 + c], d[o] * xc);
+                sacc += wb[o * 16 + c] * d[o];
+                pw[o * 16 + c] += d[o] * xc;
             }
-            dx[v * 16 + c] = __float2bfloat16_rn(s);
+            dx[v * 16 + c] = __float2bfloat16_rn(sacc);
         }
-        for (int o = 0; o < kOut; ++o) atomicAdd(&sw[kOut * 16 + o], d[o]);
     }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int e = 0; e < kOut * 16 + kOut; ++e) {
+        float t = pw[e];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) atomicAdd(&sw[e], t);
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if (lane == 0) atomicAdd(&sl, l);
     __syncthreads();
     if (threadIdx.x < kOut * 16) atomicAdd(dw + threadIdx.x, sw[threadIdx.x]);
     else if (threadIdx.x < kOut * 16 + kOut) atomicAdd(db + threadIdx.x - kOut * 16, sw[threadIdx.x]);
@@ -443,6 +630,7 @@ struct Net {
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
     float *out_norm = nullptr;
     double *loss = nullptr;
+    int *status = nullptr;         // set by a tensor-core wait that ran out
     // activations (bf16) and their gradients
     bf16 *in = nullptr;
     bf16 *act[NLAYERS] = {};
@@ -470,6 +658,7 @@ static int64_t layout(Net &net, bool assign)
     }
     net.out_norm = (float *)take((size_t)net.g[0].voxels() * kOut * 4);
     net.loss = (double *)take(8);
+    net.status = (int *)take(4);
     const int lvl[NLAYERS] = {0, 0, 1, 1, 2, 2, 3, 3, 2, 2, 1, 1, 0, 0};
     net.in = (bf16 *)take((size_t)net.g[0].voxels() * kIn * 2);
     for (int l = 0; l < NLAYERS; ++l) {
@@ -499,23 +688,42 @@ static unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) /
         if ((x) != cudaSuccess) return LBM_ECUDA;      \
     } while (0)
 
-// N tile: the largest of 64, 32, 16 that divides the output channel count
-// (16, 32, 48, 64, 96, 128 or 192); the grid covers co / BN tiles.
-static void launch_conv(const ConvArgs &a, cudaStream_t st)
+// Tensor-core convolution: K chunk = the largest of 64, 32, 16 channels that
+// divides ci; TMEM columns = the power of two >= max(32, co); a step gathers
+// 1 or 3 taps into one of two shared-memory stages (one tap of the largest
+// layer is 16 + 24 KB, for co = 192).
+constexpr int kTcMaxSmem = 96 * 1024;
+constexpr int kTcStepSmem = 48 * 1024;
+
+static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
 {
-    const int co = a.co0 + a.co1;
-    const unsigned gx = blocks(a.g.voxels(), kConvBM);
-    if (co % 64 == 0) k_conv3<64><<<dim3(gx, (unsigned)(co / 64)), 128, 0, st>>>(a);
-    else if (co % 32 == 0) k_conv3<32><<<dim3(gx, (unsigned)(co / 32)), 128, 0, st>>>(a);
-    else k_conv3<16><<<dim3(gx, (unsigned)(co / 16)), 128, 0, st>>>(a);
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem) != cudaSuccess)
+            return LBM_ECUDA;
+        attr = true;
+    }
+    const int ci = a.ci0 + a.ci1, co = a.co0 + a.co1;
+    if (ci % 16 != 0 || co % 16 != 0 || co > 256 || (a.co1 > 0 && a.co0 % 16 != 0)) return LBM_EINVAL;
+    const int kc = ci % 64 == 0 ? 64 : (ci % 32 == 0 ? 32 : 16);
+    int ncols = 32;
+    while (ncols < co) ncols <<= 1;
+    // two stages of 3 taps when they fit in kTcStepSmem, else of 1 tap.
+    // Measured on the 64x64x128 training batch: deeper pipelines (3-4 stages)
+    // and 9-tap steps were no faster or slower (they cost resident CTAs); the
+    // per-step barriers, not the gather latency, bound this kernel.
+    const size_t per_tap = (size_t)kTcM * kc * 2 + (size_t)co * kc * 2;
+    const int tp = 2 * 3 * per_tap <= (size_t)kTcStepSmem ? 3 : 1;
+    const int stages = 2;
+    k_conv3_tc<<<blocks(a.g.voxels(), kTcM), 128, stages * tp * per_tap, st>>>(a, kc, tp, ncols, stages, status);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
 static int conv(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1, int ci1, const Dims &g)
 {
     const Layer &L = net.layers[l];
     ConvArgs a{in0, ci0, in1, ci1, L.wf, net.params + L.b_off, net.act[l], L.co, nullptr, 0, 1, g};
-    launch_conv(a, net.st);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    return launch_conv(a, net.st, net.status);
 }
 
 // backward of conv layer l: mask by ReLU, weight/bias gradients, and (unless
@@ -545,7 +753,8 @@ static int conv_back(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1,
     if (dx0) {
         // input gradient: the forward kernel with flipped, transposed weights
         ConvArgs a{net.dact[l], L.co, nullptr, 0, L.wb, nullptr, dx0, ci0, dx1, ci1, 0, g};
-        launch_conv(a, net.st);
+        const int rc = launch_conv(a, net.st, net.status);
+        if (rc != LBM_OK) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
@@ -593,7 +802,7 @@ static int backward(Net &net, const float *target, float tscale)
     const Dims *g = net.g;
     UNET_TRY(cudaMemsetAsync(net.grads, 0, net.n_params * 4, net.st));
     UNET_TRY(cudaMemsetAsync(net.loss, 0, 8, net.st));
-    k_head_back<<<blocks(g[0].voxels()), 256, 0, net.st>>>(net.act[DEC1B], net.params + net.head_w, net.out_norm,
+    k_head_back<<<(unsigned)std::min<int64_t>(4 * 152, blocks(g[0].voxels())), 256, 0, net.st>>>(net.act[DEC1B], net.params + net.head_w, net.out_norm,
                                                            target, tscale, g[0], net.dact[DEC1B], net.grads + net.head_w,
                                                            net.grads + net.head_b, net.loss);
     int rc = conv_back(net, DEC1B, net.act[DEC1A], kW[0], nullptr, 0, net.dact[DEC1A], nullptr, g[0]);
@@ -683,6 +892,7 @@ int unet_bind(unet_net *net, void *dev_ws, size_t bytes, void *stream)
     layout(*net, true);
     UNET_TRY(cudaMemsetAsync(net->m, 0, net->n_params * 4, net->st));
     UNET_TRY(cudaMemsetAsync(net->v, 0, net->n_params * 4, net->st));
+    UNET_TRY(cudaMemsetAsync(net->status, 0, 4, net->st));
     net->adam_t = 0;
     return LBM_OK;
 }
@@ -721,8 +931,11 @@ int unet_backward(unet_net *net, const float *dev_target, float target_scale, do
     if (rc != LBM_OK) return rc;
     if (host_loss) {
         double s = 0.0;
+        int stalled = 0;
         UNET_TRY(cudaMemcpyAsync(&s, net->loss, 8, cudaMemcpyDeviceToHost, net->st));
+        UNET_TRY(cudaMemcpyAsync(&stalled, net->status, 4, cudaMemcpyDeviceToHost, net->st));
         UNET_TRY(cudaStreamSynchronize(net->st));
+        if (stalled) return LBM_ETIMEOUT;
         *host_loss = s / (double)(kOut * net->g[0].voxels());
     }
     return LBM_OK;
