@@ -230,6 +230,68 @@ def run_converge(args):
     print(json.dumps(line), flush=True)
 
 
+def unet_conv_flops(n, nz, ny, nx) -> float:
+    """Multiply-adds x 2 of the 3x3x3 convolutions of one forward pass
+    (27 taps x c_in x c_out per voxel of each layer's level)."""
+    from paper_1507_06565_gb300.workloads import UNET_LAYERS
+
+    level = {"enc1": 0, "enc2": 1, "enc3": 2, "bott": 3, "dec3": 2, "dec2": 1, "dec1": 0}
+    v0 = n * nz * ny * nx
+    return float(sum(2 * 27 * co * ci * v0 / 8 ** level[name[:4]] for name, co, ci in UNET_LAYERS))
+
+
+def run_unet(args):
+    """Training steps of the warm-start U-Net (forward, backward, Adam) on a
+    batch of 4 seeded 64x64x128 fields, the warm-start training shape."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    n, nz, ny, nx = 4, 128, 64, 64
+    net = L.UNet(n, nz, ny, nx, params=W.unet_init(0))
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    sdf = torch.rand((n, nz, ny, nx), device="cuda", generator=gen) * 2 - 1
+    tgt = torch.rand((n, 3, nz, ny, nx), device="cuda", generator=gen) * 0.1
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        net.forward(sdf)
+        net.backward(tgt)
+        net.adam_step(1e-3)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw = bw = 0.0
+    for _ in range(args.steps):
+        ev[0].record(stream)
+        net.forward(sdf)
+        ev[1].record(stream)
+        net.backward(tgt)
+        net.adam_step(1e-3)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fw += ev[0].elapsed_time(ev[1])
+        bw += ev[1].elapsed_time(ev[2])
+    fw, bw = fw / args.steps, bw / args.steps
+    flops = unet_conv_flops(n, nz, ny, nx)
+    try:
+        with open(PEAKS_FILE) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, kind = 1900.0, "fallback"
+    achieved = 3 * flops / ((fw + bw) * 1e-3) / 1e12
+    line = {"metric": "U-Net training step (forward, backward, Adam)", "value": 1e3 / (fw + bw),
+            "unit": "steps/s", "higher_is_better": True, "ms_per_step": fw + bw, "forward_ms": fw,
+            "backward_ms": bw, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": f"batch {n} of {nz}x{ny}x{nx} fields, 16/32/64/128 channels"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_kind": kind,
+                         "flops": "3 x forward convolution FLOPs (forward, input and weight gradients) per step"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """Time to steady state with and without the learned warm start: solver-
     generated training data, training with the library's U-Net kernels, and
@@ -437,10 +499,11 @@ def main():
                     help="neighbour indices of the odd step (library default, int32 table, row bitmasks)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
-    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "rev", "surrogate"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "rev", "surrogate", "unet"],
+                    default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
-                         "warm versus cold start")
+                         "warm versus cold start; unet: U-Net training steps")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
@@ -458,6 +521,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "unet":
+        run_unet(args)
     elif args.converge:
         run_converge(args)
     else:
