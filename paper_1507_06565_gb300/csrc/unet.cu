@@ -18,8 +18,8 @@
 // accumulator; its backward with respect to the input is the same kernel with
 // the weights flipped in the taps and transposed in the channels (the adjoint
 // of a circular/zero-padded convolution).  The weight gradient contracts over
-// voxels with warp-level MMAs (mma.sync m16n8k16) and adds block partials
-// atomically.
+// voxels on tcgen05 as well, one tap and voxel chunk per CTA, and adds the
+// partial sums atomically.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,23 +39,6 @@ constexpr int kIn = 16;       // input channels after padding
 constexpr int kOut = 3;       // velocity components
 constexpr int kW[4] = {16, 32, 64, 128};   // host-side channel widths
 constexpr int kW0 = 16;                      // first level (used in device code)
-
-// ---------------------------------------------------------------------------
-// tensor-core primitive
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
-{
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
 
 struct Dims {
     int n, d, h, w;
@@ -99,46 +82,73 @@ struct ConvArgs {
     Dims g;
 };
 
-constexpr int kPadK = 24;          // smem row length in bf16 (16 + 8 padding: conflict-free fragments)
-
 // ---------------------------------------------------------------------------
-// The convolution on the 5th-generation tensor cores (tcgen05): one CTA
-// of 128 threads computes a tile of 128 voxels x all N = co output channels
-// into a TMEM accumulator (128 lanes x N fp32 columns).  K runs over the 27
-// taps and chunks of KC input channels; each K step stages, for TP taps, the
-// gathered A tile (128 voxels x KC channels of the tap's neighbours) and the
-// B tile (N x KC weights) in shared memory with cp.async (zero-fill for voxels past the
-// end and for the zero padding in z), in 2-4 stages (two as launched), and one thread issues
-// TP*KC/16 MMAs (M=128, K=16) and commits them to the stage's mbarrier, which
-// frees the stage.  Operands are K-major without swizzle, in 8x8 core
-// matrices of 16-byte rows: core (row/8, k/8) at (row/8)*SBO + (k/8)*128 with
-// SBO = KC/8 * 128.  The epilogue reads the accumulator with tcgen05.ld
-// (warp w owns lanes 32w..32w+31, i.e. its 32 voxels), adds the bias, applies
-// the ReLU and stores bf16.  Waits on mbarriers are bounded; a wait that runs
-// out sets *a.status and the CTA still frees its TMEM.
+// Tensor-core (tcgen05) contractions of the U-Net: the 3x3x3 convolution
+// (forward and input gradient) and its weight gradient.  Both accumulate in
+// TMEM (M = 128 lanes x N fp32 columns) from bf16 operands in shared memory,
+// without swizzle, in 8x8 core matrices of 16-byte rows; a descriptor's
+// leading offset is the stride between core matrices along K and its stride
+// offset the stride between 8-row (8-element) groups along M or N, as a
+// self-checking probe of single MMAs (K-major and MN-major, M = 128)
+// confirmed.
+//
+// Pipelines (128 threads, 2-4 shared-memory stages).  Barrier-free (weight
+// gradient): every thread gathers its share of step it with cp.async into
+// stage it % stages; when its copies of step j = it - (stages - 1) have
+// landed it fences them to the async proxy and arrives on full[j % stages]
+// (128 arrivals complete a phase).  Thread 0 waits on full, issues the step's
+// MMAs and commits them to empty[j % stages]; a thread refills a stage only
+// after waiting on its empty barrier.  Two-stage with CTA barriers
+// (convolution): see pipeline_sync.  Every wait is bounded; one that runs out
+// sets *status (reported by unet_backward as LBM_ETIMEOUT) and the CTA still
+// frees its TMEM.
 // ---------------------------------------------------------------------------
 namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor (sm_100 family): start, leading (K-direction
-// core) offset, stride (8-row group) offset, all >> 4; version bit 46; no swizzle
+// shared-memory matrix descriptor (sm_100 family): start, leading offset,
+// stride offset, all >> 4; version bit 46; base offset 0; no swizzle
 __device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, both
-// K-major, N/8 at bit 17, M/16 at bit 24
-__device__ __forceinline__ uint32_t idesc(int m, int n)
+// instruction descriptor of kind::f16: f32 accumulator, bf16 A and B, N/8 at
+// bit 17, M/16 at bit 24; mn_major sets both operands MN-major (bits 15, 16)
+__device__ __forceinline__ uint32_t idesc(int m, int n, bool mn_major)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (3u << 15) : 0u) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+__device__ __forceinline__ void wait_groups(int n)
+{
+    if (n >= 3) asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+    else if (n == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id, bool acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                     tmem),
+                 "l"(ad), "l"(bd), "r"(id), "r"(acc ? 1u : 0u));
+}
+
+__device__ __forceinline__ void commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(mbar))
                  : "memory");
 }
 
@@ -153,167 +163,253 @@ __device__ __forceinline__ bool try_wait(uint32_t mbar, uint32_t parity)
 }
 
 // bounded wait: false (and *status set) if the phase did not complete
-__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity, int *status)
+__device__ __forceinline__ bool wait(uint64_t *mbar, uint32_t parity, int *status)
 {
+    const uint32_t a = smem_u32(mbar);
     for (int it = 0; it < (1 << 24); ++it)
-        if (try_wait(mbar, parity)) return true;
+        if (try_wait(a, parity)) return true;
     atomicExch(status, 1);
     return false;
+}
+
+__device__ __forceinline__ void arrive(uint64_t *mbar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+constexpr int kMaxStages = 4;
+
+// Shared set-up: TMEM columns and the full/empty barriers.
+struct Ctx {
+    uint64_t *full, *empty;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ void setup(uint32_t *tmem_slot, uint64_t *full, uint64_t *empty, int stages, int ncols)
+{
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < stages; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[q])), "r"(128));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])));
+        }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// The producer/consumer loop.  fill(it, s) issues this thread's cp.async
+// copies of step it into stage s (no commit); issue(j, s) issues step j's MMAs
+// (thread 0 only).  Returns true (on every thread) when all MMAs completed.
+template <class Fill, class Issue>
+__device__ __forceinline__ bool pipeline(int iters, int stages, uint64_t *full, uint64_t *empty, int *status,
+                                         Fill fill, Issue issue)
+{
+    const int lag = stages - 1;
+    bool ok = true;
+    for (int it = 0; it < iters + lag && ok; ++it) {
+        if (it < iters) {
+            const int s = it % stages;
+            // the MMAs of step it - stages read this stage; they were issued
+            // at step it - 1 of thread 0
+            if (it >= stages) ok = wait(&empty[s], (uint32_t)((it / stages - 1) & 1), status);
+            if (!ok) break;
+            fill(it, s);
+        }
+        commit_group();   // one group per step (empty while draining)
+        if (it >= lag) {
+            const int j = it - lag, s = j % stages;
+            wait_groups(lag);   // this thread's copies of step j have landed
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            arrive(&full[s]);
+            if (threadIdx.x == 0) {
+                ok = wait(&full[s], (uint32_t)((j / stages) & 1), status);
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    issue(j, s);
+                    commit(&empty[s]);
+                }
+            }
+        }
+    }
+    wait_groups(0);
+    int w = ok ? 1 : 0;
+    if (threadIdx.x == 0 && ok) {
+        // the last commit tracks every MMA issued before it
+        const int l = iters - 1;
+        w = wait(&empty[l % stages], (uint32_t)((l / stages) & 1), status) ? 1 : 0;
+    }
+    ok = __syncthreads_and(w) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    return ok;
+}
+
+// Two-stage variant with CTA barriers: the whole CTA gathers step it, waits
+// for its copies of step it - 1, and thread 0 issues that step after a
+// barrier.  Used by the convolution, where it measured faster than the
+// barrier-free loop (its steps are short and its producer shares uniform).
+template <class Fill, class Issue>
+__device__ __forceinline__ bool pipeline_sync(int iters, uint64_t *empty, int *status, Fill fill, Issue issue)
+{
+    bool ok = true;
+    for (int it = 0; it < iters; ++it) {
+        const int s = it & 1;
+        if (it >= 2) {
+            // thread 0 waits for the MMAs that last read stage s; the barrier
+            // hands its verdict to the whole CTA
+            int w = 1;
+            if (threadIdx.x == 0) w = wait(&empty[s], (uint32_t)(((it - 2) >> 1) & 1), status) ? 1 : 0;
+            ok = __syncthreads_and(w) != 0;
+            if (!ok) break;
+        }
+        fill(it, s);
+        commit_group();
+        if (it >= 1) {
+            wait_groups(1);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                issue(it - 1, (it - 1) & 1);
+                commit(&empty[(it - 1) & 1]);
+            }
+        }
+    }
+    wait_groups(0);
+    int w = ok ? 1 : 0;
+    if (ok) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int l = iters - 1;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            issue(l, l & 1);
+            commit(&empty[l & 1]);
+            // the last commit tracks every MMA issued before it
+            w = wait(&empty[l & 1], (uint32_t)((l >> 1) & 1), status) ? 1 : 0;
+        }
+    } else {
+        __syncthreads();
+    }
+    ok = __syncthreads_and(w) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    return ok;
+}
+
+__device__ __forceinline__ void teardown(uint32_t tmem, int ncols)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+}
+
+// 16 fp32 accumulator columns c0..c0+15 of lane 32w + (thread's lane)
+__device__ __forceinline__ void load16(uint32_t tmem, int warp, int c0, uint32_t r[16])
+{
+    const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// voxel v -> (n, z, y, x) and the tap-t neighbour (-1 outside z); 32-bit
+// arithmetic (the host keeps voxel counts below 2^31)
+__device__ __forceinline__ int32_t tap_nb(const Dims &g, int32_t v, int dz, int dy, int dx)
+{
+    const int x = v % g.w;
+    int32_t r = v / g.w;
+    const int y = r % g.h;
+    r /= g.h;
+    const int z = r % g.d;
+    const int32_t n = r / g.d;
+    const int zz = z + dz;
+    if (zz < 0 || zz >= g.d) return -1;
+    int yy = y + dy, xx = x + dx;
+    yy = yy < 0 ? yy + g.h : (yy >= g.h ? yy - g.h : yy);
+    xx = xx < 0 ? xx + g.w : (xx >= g.w ? xx - g.w : xx);
+    return ((n * g.d + zz) * g.h + yy) * g.w + xx;
 }
 
 }  // namespace tc
 
 constexpr int kTcM = 128;
-constexpr int kTcMaxStages = 4;
 
+// ---------------------------------------------------------------------------
+// Convolution: one CTA computes 128 voxels x all N = co output channels.  K
+// runs over the 27 taps and chunks of KC input channels (the largest of 64,
+// 32, 16 dividing ci); a step gathers 1 or 3 taps: A = 128 voxels x KC channels
+// of the tap's neighbours (circular in x, y; zero in z and past the end), B =
+// N x KC weights, both K-major (core (row/8, k/8) at (row/8)*SBO + (k/8)*128,
+// SBO = KC/8 * 128).  Thread t gathers row t of A and a share of B.  The
+// epilogue reads TMEM with tcgen05.ld (warp w owns voxels 32w..32w+31), adds
+// the bias, applies ReLU and stores bf16.  The input gradient is the same
+// kernel with the weights flipped in the taps and transposed in the channels.
+// Its steps run through the two-stage pipeline with CTA barriers.
+// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, int ncols, int stages, int *status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[kTcMaxStages];
-    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t full[tc::kMaxStages], empty[tc::kMaxStages];
+    __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ci = a.ci0 + a.ci1, n = a.co0 + a.co1;
-    const int64_t V = a.g.voxels();
-    const int64_t m0 = (int64_t)blockIdx.x * kTcM;
-    // a step gathers tp taps x kc channels: tp A sub-tiles, then tp B sub-tiles
+    const int32_t V = (int32_t)a.g.voxels();
+    const int32_t m0 = (int32_t)blockIdx.x * kTcM;
+    // a step gathers tp taps: tp A sub-tiles, then tp B sub-tiles
     const uint32_t a_bytes = (uint32_t)kTcM * kc * 2, b_bytes = (uint32_t)n * kc * 2;
     const uint32_t stage_bytes = (uint32_t)tp * (a_bytes + b_bytes), sbo = (uint32_t)(kc / 8) * 128u;
     const uint32_t base = tc::smem_u32(smem);
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                         tc::smem_u32(&tmem_base)), "r"(ncols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-    }
-    if (tid == 0)
-        for (int q = 0; q < stages; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::smem_u32(&mbar[q])));
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = tmem_base;
-
-    // this thread's voxel (row tid of the tile) and its coordinates
-    const int64_t v = m0 + tid;
+    tc::setup(&tmem_slot, full, empty, stages, ncols);
+    const uint32_t tmem = tmem_slot;
+    const int32_t v = m0 + tid;
     const bool vin = v < V;
-    int x = 0, y = 0, z = 0;
-    int64_t nn = 0;
-    if (vin) {
-        x = (int)(v % a.g.w);
-        int64_t r = v / a.g.w;
-        y = (int)(r % a.g.h);
-        r /= a.g.h;
-        z = (int)(r % a.g.d);
-        nn = r / a.g.d;
-    }
     const int chunks = ci / kc, iters = (kTaps / tp) * chunks;
-    const uint32_t id = tc::idesc(kTcM, n);
-    bool ok = true;
+    const uint32_t id = tc::idesc(kTcM, n, false);
+    const uint32_t row_off = (uint32_t)(tid >> 3) * sbo + (uint32_t)(tid & 7) * 16u;
 
     auto fill = [&](int it, int s) {
         const int tg = it / chunks, c0 = (it % chunks) * kc;
-        const uint32_t row_off = (uint32_t)(tid >> 3) * sbo + (uint32_t)(tid & 7) * 16u;
         for (int q = 0; q < tp; ++q) {
             const int t = tg * tp + q;
             const uint32_t sa = base + (uint32_t)s * stage_bytes + (uint32_t)q * a_bytes;
             const uint32_t sb = base + (uint32_t)s * stage_bytes + (uint32_t)tp * a_bytes + (uint32_t)q * b_bytes;
-            // A: row tid, kc/8 chunks of 8 channels of the tap's neighbour
-            const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            const int zz = z + dz;
-            const bool valid = vin && zz >= 0 && zz < a.g.d;
-            int yy = y + dy, xx = x + dx;
-            yy = yy < 0 ? yy + a.g.h : (yy >= a.g.h ? yy - a.g.h : yy);
-            xx = xx < 0 ? xx + a.g.w : (xx >= a.g.w ? xx - a.g.w : xx);
-            const int64_t nb = valid ? ((nn * a.g.d + zz) * a.g.h + yy) * a.g.w + xx : 0;
+            const int32_t nb = vin ? tc::tap_nb(a.g, v, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1) : -1;
+            const bool valid = nb >= 0;
             for (int j = 0; j < kc / 8; ++j) {
                 const int c = c0 + 8 * j;
-                const bf16 *src = c < a.ci0 ? a.in0 + nb * a.ci0 + c : a.in1 + nb * a.ci1 + (c - a.ci0);
+                const bf16 *src =
+                    c < a.ci0 ? a.in0 + (int64_t)nb * a.ci0 + c : a.in1 + (int64_t)nb * a.ci1 + (c - a.ci0);
                 tc::cp16(sa + row_off + (uint32_t)j * 128u, valid ? (const void *)src : (const void *)a.in0, valid);
             }
-            // B: n rows x kc/8 chunks of the tap's weights
             for (int e = tid; e < n * (kc / 8); e += 128) {
                 const int r = e / (kc / 8), j = e % (kc / 8);
                 const bf16 *src = a.w + ((int64_t)t * n + r) * ci + c0 + 8 * j;
                 tc::cp16(sb + (uint32_t)(r >> 3) * sbo + (uint32_t)j * 128u + (uint32_t)(r & 7) * 16u, src, true);
             }
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
     auto issue = [&](int it, int s) {
         for (int q = 0; q < tp; ++q) {
             const uint32_t sa = base + (uint32_t)s * stage_bytes + (uint32_t)q * a_bytes;
             const uint32_t sb = base + (uint32_t)s * stage_bytes + (uint32_t)tp * a_bytes + (uint32_t)q * b_bytes;
-            for (int j = 0; j < kc / 16; ++j) {
-                const uint64_t ad = tc::desc(sa + (uint32_t)j * 256u, 128u, sbo);
-                const uint64_t bd = tc::desc(sb + (uint32_t)j * 256u, 128u, sbo);
-                const uint32_t acc = (it > 0 || q > 0 || j > 0) ? 1u : 0u;
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                             "l"(ad), "l"(bd), "r"(id), "r"(acc));
-            }
+            for (int j = 0; j < kc / 16; ++j)
+                tc::mma(tmem, tc::desc(sa + (uint32_t)j * 256u, 128u, sbo),
+                        tc::desc(sb + (uint32_t)j * 256u, 128u, sbo), id, it > 0 || q > 0 || j > 0);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         tc::smem_u32(&mbar[s]))
-                     : "memory");
     };
-
-    // step it: (1) wait until the MMAs of step it - stages, which read stage
-    // it % stages, are done; (2) gather step it into that stage; (3) once the
-    // gather of step it - (stages - 1) has landed, issue its MMAs.  A gather
-    // thus has stages - 1 steps to arrive and an MMA one step to finish.
-    const int lag = stages - 1;
-    for (int it = 0; it < iters; ++it) {
-        const int s = it % stages;
-        if (it >= stages) {
-            // thread 0 waits; the barrier hands its verdict to the whole CTA
-            int w = 1;
-            if (tid == 0) w = tc::wait(tc::smem_u32(&mbar[s]), (uint32_t)((it / stages - 1) & 1), status) ? 1 : 0;
-            ok = __syncthreads_and(w) != 0;
-            if (!ok) break;
-        }
-        fill(it, s);
-        if (it >= lag) {
-            if (lag == 3) asm volatile("cp.async.wait_group 3;\n" ::: "memory");
-            else if (lag == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-            else asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                issue(it - lag, (it - lag) % stages);
-            }
-        }
-    }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    const bool ok = tc::pipeline_sync(iters, empty, status, fill, issue);
     if (ok) {
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        int w = 1;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            for (int j = iters - lag; j < iters; ++j) issue(j, j % stages);
-            // the last commit tracks every MMA issued before it
-            const int l = iters - 1;
-            w = tc::wait(tc::smem_u32(&mbar[l % stages]), (uint32_t)((l / stages) & 1), status) ? 1 : 0;
-        }
-        ok = __syncthreads_and(w) != 0;
-    } else {
-        __syncthreads();
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (ok) {
-        // epilogue: warp w reads its 32 lanes (voxels), 16 columns at a time
-        const int64_t row = m0 + warp * 32 + lane;
+        const int32_t row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < n; c0 += 16) {
             uint32_t r[16];
-            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];\n"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(addr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            tc::load16(tmem, warp, c0, r);
             if (row < V) {
                 uint32_t packed[8];
 #pragma unroll
@@ -329,21 +425,27 @@ __global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, in
                     packed[j] = *reinterpret_cast<const uint32_t *>(&pr);
                 }
                 // 16 channels lie in one of the two outputs (co0 is a multiple of 16)
-                bf16 *dst = c0 < a.co0 ? a.out0 + row * a.co0 + c0 : a.out1 + row * a.co1 + (c0 - a.co0);
+                bf16 *dst = c0 < a.co0 ? a.out0 + (int64_t)row * a.co0 + c0 : a.out1 + (int64_t)row * a.co1 + (c0 - a.co0);
                 uint4 *d4 = reinterpret_cast<uint4 *>(dst);
                 d4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
                 d4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+    tc::teardown(tmem, ncols);
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient: dW[t][o][c] += sum_v dY[v][o] X(v + off_t)[c]
-// (M = output channels, N = 16 input channels per block, K = voxels)
+// Weight gradient dW[t][o][c] += sum_v dY[v][o] X(v + off_t)[c]: one CTA per
+// (voxel chunk, tap) computes D = dY^T X_t with M = 128 rows (o < co used),
+// N = ci, K = the chunk's voxels in steps of kWgStepVox, and adds D to dW with
+// fp32 atomics.  Both operands are MN-major: for each voxel, A holds dY's co
+// channels (a plain row of dY) and B the neighbour's ci channels; element
+// (mn, k) at (mn/8)*SBO + (k/8)*128 + (k%8)*16 + (mn%8)*2 with SBO =
+// kWgStepVox * 16.  Only the co/8 groups of A that exist are written: the MMA
+// also reads rows co..127, which land in the following shared memory (held
+// inside the allocation by a tail pad) and reach only accumulator rows that
+// are never read.
 // ---------------------------------------------------------------------------
 struct WgradArgs {
     const bf16 *dy;
@@ -354,70 +456,70 @@ struct WgradArgs {
     int ci1;
     float *dw;          // [27][co][ci] fp32 (accumulated)
     Dims g;
-    int chunk;          // voxels per block
+    int chunk;          // voxels per CTA (a multiple of kWgStepVox)
 };
 
-template <int BM>
-__global__ void __launch_bounds__(32 * (BM / 16)) k_wgrad(WgradArgs a)
+constexpr int kWgStepVox = 64;
+constexpr uint32_t kWgSbo = kWgStepVox * 16;              // bytes per 8-element MN group
+constexpr uint32_t kWgTail = (kTcM / 8) * kWgSbo;          // over-read room for A
+
+__global__ void __launch_bounds__(128) k_wgrad_tc(WgradArgs a, int ncols, int stages, int *status)
 {
-    __shared__ __align__(16) bf16 Ys[16][BM + 8];
-    __shared__ __align__(16) bf16 Xs[16][kPadK];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-    const int nthreads = 32 * (BM / 16);
-    const int o0 = blockIdx.y * BM, c0 = blockIdx.z * 16;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[tc::kMaxStages], empty[tc::kMaxStages];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int co = a.co, ci = a.ci0 + a.ci1;
+    const int32_t V = (int32_t)a.g.voxels();
     const int t = (int)(blockIdx.x % kTaps);
-    const int64_t v_begin = (int64_t)(blockIdx.x / kTaps) * a.chunk;
-    const int64_t V = a.g.voxels();
-    const int64_t v_end = v_begin + a.chunk < V ? v_begin + a.chunk : V;
-    const int ci = a.ci0 + a.ci1;
-    float acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-    for (int64_t vb = v_begin; vb < v_end; vb += 16) {
-        // stage dY[vb..vb+16][o0..o0+BM] and X(v + off)[c0..c0+16]
-        for (int e = tid; e < 16 * (BM / 8); e += nthreads) {
-            const int r = e / (BM / 8), q = e % (BM / 8);
-            const int64_t v = vb + r;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (v < v_end && o0 + 8 * q < a.co) val = *reinterpret_cast<const uint4 *>(a.dy + v * a.co + o0 + 8 * q);
-            *reinterpret_cast<uint4 *>(&Ys[r][8 * q]) = val;
+    const int32_t v_begin = (int32_t)(blockIdx.x / kTaps) * a.chunk;
+    const uint32_t a_bytes = (uint32_t)(co / 8) * kWgSbo, b_bytes = (uint32_t)(ci / 8) * kWgSbo;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const uint32_t base = tc::smem_u32(smem);
+    tc::setup(&tmem_slot, full, empty, stages, ncols);
+    const uint32_t tmem = tmem_slot;
+    const uint32_t id = tc::idesc(kTcM, ci, true);
+    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const int iters = a.chunk / kWgStepVox;
+    // thread t handles voxel k = t % 64 of each step, pieces part, part + 2, ...
+    const int k = tid % kWgStepVox, part = tid / kWgStepVox;
+    const uint32_t k_off = (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 16u;
+
+    auto fill = [&](int it, int s) {
+        const uint32_t sa = base + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
+        const int32_t v = v_begin + it * kWgStepVox + k;
+        const bool vin = v < V;
+        for (int mg = part; mg < co / 8; mg += 2)
+            tc::cp16(sa + (uint32_t)mg * kWgSbo + k_off,
+                     vin ? (const void *)(a.dy + (int64_t)v * co + 8 * mg) : (const void *)a.dy, vin);
+        const int32_t nb = vin ? tc::tap_nb(a.g, v, dz, dy, dx) : -1;
+        const bool valid = nb >= 0;
+        for (int ng = part; ng < ci / 8; ng += 2) {
+            const int c = 8 * ng;
+            const bf16 *src = c < a.ci0 ? a.in0 + (int64_t)nb * a.ci0 + c : a.in1 + (int64_t)nb * a.ci1 + (c - a.ci0);
+            tc::cp16(sb + (uint32_t)ng * kWgSbo + k_off, valid ? (const void *)src : (const void *)a.in0, valid);
         }
-        if (tid < 32) {
-            const int r = tid >> 1, half = tid & 1;
-            const int64_t v = vb + r;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (v < v_end) {
-                const int64_t nb = tap_neighbour(a.g, v, t);
-                if (nb >= 0) {
-                    const bf16 *src = c0 < a.ci0 ? a.in0 + nb * a.ci0 + c0 : a.in1 + nb * a.ci1 + (c0 - a.ci0);
-                    val = *reinterpret_cast<const uint4 *>(src + 8 * half);
-                }
+    };
+    auto issue = [&](int it, int s) {
+        const uint32_t sa = base + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
+        for (int j = 0; j < kWgStepVox / 16; ++j)
+            tc::mma(tmem, tc::desc(sa + (uint32_t)j * 256u, 128u, kWgSbo), tc::desc(sb + (uint32_t)j * 256u, 128u, kWgSbo),
+                    id, it > 0 || j > 0);
+    };
+    const bool ok = tc::pipeline(iters, stages, full, empty, status, fill, issue);
+    if (ok && warp * 32 < co) {
+        const int o = warp * 32 + lane;
+        for (int c0 = 0; c0 < ci; c0 += 16) {
+            uint32_t r[16];
+            tc::load16(tmem, warp, c0, r);
+            if (o < co) {
+                float *dst = a.dw + ((int64_t)t * co + o) * ci + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) atomicAdd(dst + j, __uint_as_float(r[j]));
             }
-            *reinterpret_cast<uint4 *>(&Xs[r][8 * half]) = val;
         }
-        __syncthreads();
-        // A (rows o, cols v) = Ys[v][o]; B (rows v, cols c) = Xs[v][c]
-        const int o = warp * 16 + g;
-        uint32_t af[4];
-        af[0] = pack2(Ys[2 * t4][o], Ys[2 * t4 + 1][o]);
-        af[1] = pack2(Ys[2 * t4][o + 8], Ys[2 * t4 + 1][o + 8]);
-        af[2] = pack2(Ys[2 * t4 + 8][o], Ys[2 * t4 + 9][o]);
-        af[3] = pack2(Ys[2 * t4 + 8][o + 8], Ys[2 * t4 + 9][o + 8]);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            uint32_t bfr[2];
-            bfr[0] = pack2(Xs[2 * t4][8 * j + g], Xs[2 * t4 + 1][8 * j + g]);
-            bfr[1] = pack2(Xs[2 * t4 + 8][8 * j + g], Xs[2 * t4 + 9][8 * j + g]);
-            mma_bf16(acc[j], af, bfr);
-        }
-        __syncthreads();
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int o = o0 + warp * 16 + g + 8 * (e >> 1);
-            const int c = c0 + 8 * j + 2 * t4 + (e & 1);
-            if (o < a.co && c < ci) atomicAdd(a.dw + ((int64_t)t * a.co + o) * ci + c, acc[j][e]);
-        }
+    tc::teardown(tmem, ncols);
 }
 
 // bias gradient: db[o] += sum_v dY[v][o]
@@ -688,12 +790,11 @@ static unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) /
         if ((x) != cudaSuccess) return LBM_ECUDA;      \
     } while (0)
 
-// Tensor-core convolution: K chunk = the largest of 64, 32, 16 channels that
-// divides ci; TMEM columns = the power of two >= max(32, co); a step gathers
-// 1 or 3 taps into one of two shared-memory stages (one tap of the largest
-// layer is 16 + 24 KB, for co = 192).
+// Shared memory of the tensor-core kernels: stages are added (2..4) while
+// they fit in kTcStepSmem; one stage of the largest layer (co = 192, KC = 64)
+// is 40 KB, so two of them (80 KB) stay within kTcMaxSmem.
 constexpr int kTcMaxSmem = 96 * 1024;
-constexpr int kTcStepSmem = 48 * 1024;
+constexpr int kTcStepSmem = 64 * 1024;
 
 static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
 {
@@ -704,16 +805,18 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
         attr = true;
     }
     const int ci = a.ci0 + a.ci1, co = a.co0 + a.co1;
-    if (ci % 16 != 0 || co % 16 != 0 || co > 256 || (a.co1 > 0 && a.co0 % 16 != 0)) return LBM_EINVAL;
+    if (ci % 16 != 0 || co % 16 != 0 || co > 256 || (a.co1 > 0 && a.co0 % 16 != 0) ||
+        a.g.voxels() >= ((int64_t)1 << 31))
+        return LBM_EINVAL;
     const int kc = ci % 64 == 0 ? 64 : (ci % 32 == 0 ? 32 : 16);
     int ncols = 32;
     while (ncols < co) ncols <<= 1;
-    // two stages of 3 taps when they fit in kTcStepSmem, else of 1 tap.
-    // Measured on the 64x64x128 training batch: deeper pipelines (3-4 stages)
-    // and 9-tap steps were no faster or slower (they cost resident CTAs); the
-    // per-step barriers, not the gather latency, bound this kernel.
+    // two stages of 3 taps when they fit in 48 KB, else of 1 tap.  Measured on
+    // the 64x64x128 training batch: the barrier-free loop, 3-4 stages and
+    // 9-tap steps were all slower (they cost resident CTAs or add per-step
+    // work); the gathers, not the tensor cores, bound this kernel.
     const size_t per_tap = (size_t)kTcM * kc * 2 + (size_t)co * kc * 2;
-    const int tp = 2 * 3 * per_tap <= (size_t)kTcStepSmem ? 3 : 1;
+    const int tp = 2 * 3 * per_tap <= (size_t)48 * 1024 ? 3 : 1;
     const int stages = 2;
     k_conv3_tc<<<blocks(a.g.voxels(), kTcM), 128, stages * tp * per_tap, st>>>(a, kc, tp, ncols, stages, status);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
@@ -734,18 +837,31 @@ static int conv_back(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1,
     Layer &L = net.layers[l];
     const int64_t V = g.voxels();
     k_relu_back<<<blocks(V * L.co), 256, 0, net.st>>>(net.dact[l], net.act[l], V * L.co);
-    // weight gradient: grid x = (voxel chunk, tap), y = output-channel tile,
-    // z = input-channel tile (x has no 65535 limit; y, z stay below 16)
-    const int chunk = 512;
-    WgradArgs wa{net.dact[l], L.co, in0, ci0, in1, ci1, net.grads + L.w_off, g, chunk};
-    const unsigned nchunk = blocks(V, chunk);
-    const unsigned cit = (unsigned)((ci0 + ci1) / 16);
-    if (L.co >= 64) {
-        k_wgrad<64><<<dim3(nchunk * kTaps, (unsigned)(L.co / 64), cit), 128, 0, net.st>>>(wa);
-    } else if (L.co == 32) {
-        k_wgrad<32><<<dim3(nchunk * kTaps, 1, cit), 64, 0, net.st>>>(wa);
-    } else {
-        k_wgrad<16><<<dim3(nchunk * kTaps, 1, cit), 32, 0, net.st>>>(wa);
+    // weight gradient on the tensor cores: one CTA per (voxel chunk, tap) on
+    // grid x; chunks of 128..4096 voxels (a power of two) so that the grid
+    // keeps ~16 CTAs per SM busy
+    {
+        static bool attr = false;
+        if (!attr) {
+            if (cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem) !=
+                cudaSuccess)
+                return LBM_ECUDA;
+            attr = true;
+        }
+        const int ci = ci0 + ci1;
+        if (L.co > kTcM || L.co % 16 != 0 || ci % 16 != 0 || ci > 256 || V >= ((int64_t)1 << 31))
+            return LBM_EINVAL;
+        int chunk = 4096;
+        while (chunk > 128 && (int64_t)kTaps * ((V + chunk - 1) / chunk) < 16 * 152) chunk >>= 1;
+        WgradArgs wa{net.dact[l], L.co, in0, ci0, in1, ci1, net.grads + L.w_off, g, chunk};
+        int ncols = 32;
+        while (ncols < ci) ncols <<= 1;
+        const size_t stage = (size_t)(L.co / 8 + ci / 8) * kWgSbo;
+        int stages = tc::kMaxStages;
+        while (stages > 2 && stages * stage + kWgTail > (size_t)kTcStepSmem) --stages;
+        k_wgrad_tc<<<(unsigned)(blocks(V, chunk) * kTaps), 128, stages * stage + kWgTail, net.st>>>(wa, ncols, stages,
+                                                                                                    net.status);
+        if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     }
     const int lanes = 256 / L.co;
     k_bias_grad<<<(unsigned)std::min<int64_t>(1024, blocks(V, lanes)), lanes * L.co, lanes * L.co * 4, net.st>>>(
