@@ -30,7 +30,7 @@ def _rank(rank, world, port, out):
 
 def test_two_ranks_take_the_slowest_time():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0] == out[1]
     ms, rate = out[0]
