@@ -65,6 +65,7 @@ def _load():
         "orc_rates": (None, [_d, _d, _p, _p, _p]),
         "orc_equilibrium": (None, [_d, _p, _p]),
         "orc_lbm_create": (_p, [_i, _i, _i, _i, _d, _d, _p, _i64, _d, _d, _d, _d, _d]),
+        "orc_lbm_set_simple_bounce_back": (None, [_p]),
         "orc_lbm_destroy": (None, [_p]),
         "orc_lbm_init": (None, [_p, _p]),
         "orc_lbm_step": (None, [_p, _i64]),
@@ -196,7 +197,7 @@ class Lattice:
     """Dense two-array FP64 TRT/CLI lattice; fields are [.., nz, ny, nx]."""
 
     def __init__(self, nx, ny, nz, periodic_z, xyzr=(), tau=0.8, lam=3.0 / 16.0, g=(1e-6, 0.0, 0.0),
-                 q_lo=0.5, q_hi=0.5):
+                 q_lo=0.5, q_hi=0.5, simple_bounce_back=False):
         self._lib = _load()
         sp = np.ascontiguousarray(np.asarray(xyzr, np.float64).reshape(-1, 4))
         self.shape = (nz, ny, nx)
@@ -206,6 +207,8 @@ class Lattice:
                                            sp.shape[0], tau, lam, *self.g)
         if not self._h:
             raise MemoryError("oracle lattice allocation failed")
+        if simple_bounce_back:
+            self._lib.orc_lbm_set_simple_bounce_back(self._h)
         self.nu = float(self._lib.orc_lbm_nu(self._h))
 
     def __del__(self):

@@ -620,6 +620,14 @@ void orc_equilibrium(double rho, const double *u, double *feq)
     }
 }
 
+/* Simple bounce-back (Eq. (noslip)) on every wall link: a = 0, i.e. the
+ * wall half-way along each link whatever its q.  Call before stepping. */
+void orc_lbm_set_simple_bounce_back(orc_lbm *s)
+{
+    const int64_t nl = s->link_start[s->ncell];
+    for (int64_t l = 0; l < nl; ++l) s->link_a[l] = 0.0;
+}
+
 /* Initial state f_k = f_k^eq(rho = 1, u0); u0 is [3][ncell] or NULL (rest). */
 void orc_lbm_init(orc_lbm *s, const double *u0)
 {

@@ -86,8 +86,8 @@ def test_splitmix64_published_outputs():
 # for the velocity u = j + g/2.  With q = 1/2 (Eq. (noslip)) and
 # Lambda = 3/16 it vanishes: the exact half-way wall quoted in Sec. 2.1.
 # ---------------------------------------------------------------------------
-def _channel(nz, tau, lam, q_lo, q_hi, g=1e-6):
-    lat = O.Lattice(2, 2, nz, False, (), tau, lam, (g, 0.0, 0.0), q_lo, q_hi).init()
+def _channel(nz, tau, lam, q_lo, q_hi, g=1e-6, simple_bounce_back=False):
+    lat = O.Lattice(2, 2, nz, False, (), tau, lam, (g, 0.0, 0.0), q_lo, q_hi, simple_bounce_back).init()
     H = nz - 2
     lat.step(int(40 * H * H / (math.pi ** 2 * lat.nu)) + 200)
     _, u = lat.moments()
@@ -119,6 +119,27 @@ def test_poiseuille_half_way_exact(tau):
 ])
 def test_channel_wall_slip_closed_form(tau, lam, q_lo, q_hi):
     lat, ux, exact, _ = _channel(18, tau, lam, q_lo, q_hi)
+    assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
+
+
+def test_channel_srt_closed_form():
+    """SRT is TRT with Lambda = (tau - 1/2)^2 (omega- = omega+); the wall-slip
+    closed form holds for it too (bounce-back walls slip by -(g/nu)(1/8 -
+    2 Lambda/3), which is not zero for SRT)."""
+    tau = 1.2
+    lam = (tau - 0.5) ** 2
+    _, ux, exact, _ = _channel(18, tau, lam, 0.5, 0.5)
+    assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
+    _, ux, exact, _ = _channel(18, tau, lam, 0.3, 0.8)
+    assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
+
+
+def test_simple_bounce_back_places_walls_half_way():
+    """With simple bounce-back forced on every link (Eq. (noslip)), off-grid
+    walls (q = 0.3, 0.8) act as half-way walls: the profile is that of
+    q = 1/2."""
+    _, ux, _, _ = _channel(18, 0.8, 3 / 16, 0.3, 0.8, simple_bounce_back=True)
+    _, _, exact, _ = _channel(18, 0.8, 3 / 16, 0.5, 0.5)
     assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
 
 
