@@ -164,8 +164,24 @@ def cpu_baseline(seconds_hint: float = 15.0):
     t0 = time.perf_counter()
     lat.step(n)
     dt = time.perf_counter() - t0
-    return {"value": nf * n / dt / 1e6, "unit": "MLUPS", "cores": O.threads(), "kind": "oracle",
-            "sample": f"{SAMPLE.name} ({nf} fluid cells), FP64 dense two-array oracle, {n} steps after 1 warm-up"}
+    cores = O.threads()
+    # the same oracle on one core, over the small sample, for a few seconds
+    O.set_threads(1)
+    try:
+        sp1, _, _ = O.place_spheres(*SAMPLE_STEP.sphere_args())
+        lat1 = O.Lattice(SAMPLE_STEP.nx, SAMPLE_STEP.ny, SAMPLE_STEP.nz, False, sp1, SAMPLE_STEP.tau, SAMPLE_STEP.lam,
+                         SAMPLE_STEP.g).init()
+        nf1 = int((lat1.solid() == 0).sum())
+        lat1.step(1)
+        t1 = time.perf_counter()
+        lat1.step(3)
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(cores)
+    return {"value": nf * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{SAMPLE.name} ({nf} fluid cells), FP64 dense two-array oracle, {n} steps after 1 warm-up",
+            "single_core": {"value": nf1 * 3 / dt1 / 1e6, "unit": "MLUPS", "cores": 1,
+                            "sample": f"{SAMPLE_STEP.name} ({nf1} fluid cells), 3 steps after 1 warm-up"}}
 
 
 def workload_name(args):
@@ -174,6 +190,9 @@ def workload_name(args):
     if args.workload == "channel-half":
         return (WORKLOAD.replace("256x256x512", "128x128x256").replace("z=0/511", "z=0/255")
                 .replace("z<256", "z<128"))
+    if args.workload == "w0":
+        return ("151^3 periodic cube, one centred sphere of diameter 90 (the paper's per-core block), "
+                + ("simple bounce-back on every link" if args.bounce_back else "CLI walls"))
     if args.workload == "large":
         return ("512x512x1024 channel, walls z=0/1023, porous layer z<512 of overlapping r=8 spheres, porosity 0.6 "
                 "(seed 3060); one step = one time step of the box")
@@ -184,8 +203,11 @@ def workload_name(args):
 def odd_flags(args) -> int:
     import paper_1507_06565_gb300 as L
 
-    return {"auto": 0, "table": L.LBM_FLAG_NEIGHBOUR_TABLE,
-            "rows": L.LBM_FLAG_ROW_NEIGHBOURS}[getattr(args, "odd", "auto")]
+    flags = {"auto": 0, "table": L.LBM_FLAG_NEIGHBOUR_TABLE,
+             "rows": L.LBM_FLAG_ROW_NEIGHBOURS}[getattr(args, "odd", "auto")]
+    if getattr(args, "bounce_back", False):
+        flags |= L.LBM_FLAG_SIMPLE_BOUNCE_BACK
+    return flags
 
 
 def run_converge(args):
@@ -204,9 +226,7 @@ def run_converge(args):
         geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
         solvers = [L.BatchSolver(geoms, cases[0].tau, cases[0].lam, cases[0].g, args.storage, flags=odd_flags(args))]
     else:
-        cases = [W.W2(phi) for phi in W.W2_POROSITIES] if args.workload == "channel" else [
-            W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True, W.W2(phi).seed)
-            for phi in W.W2_POROSITIES]
+        cases = [W.W2(phi) if args.workload == "channel" else W.W2_half(phi) for phi in W.W2_POROSITIES]
         geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
         solvers = [L.Solver(g, c.tau, c.lam, c.g, args.storage, flags=odd_flags(args)) for g, c in zip(geoms, cases)]
     out = []
@@ -218,12 +238,17 @@ def run_converge(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         total_s += dt
+        rec = {}
         if isinstance(s, L.BatchSolver):
             k = s.permeabilities().tolist()
         else:
             k = [s.permeability(*c.perm_window)]
+            # plane-averaged superficial u_x and porosity, every 8th plane (Sec. 3.1 profiles)
+            pa = s.plane_average()
+            rec = {"profile_z_every8": list(range(0, c.nz, 8)), "u_sup_every8": pa[::8, 0].tolist(),
+                   "porosity_every8": pa[::8, 2].tolist()}
         out.append({"status": L.status_string(rc), "steps": n, "residual": res, "seconds": dt,
-                    "mlups": s.info()["n_fluid"] * n / dt / 1e6, "permeability": k, "schedule": s.schedule()})
+                    "mlups": s.info()["n_fluid"] * n / dt / 1e6, "permeability": k, "schedule": s.schedule(), **rec})
     line = {"metric": f"time to steady state (plane-profile residual < {args.tol:g})", "value": total_s, "unit": "s",
             "higher_is_better": False, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": workload_name(args)}, "runs": out}
@@ -362,13 +387,17 @@ def run_ours(args, world, rank, local):
     if args.workload == "channel":
         cases = [W.W2(phi) for phi in W.W2_POROSITIES]
     elif args.workload == "channel-half":   # the same channel at half the size, for profiler captures
-        cases = [W.Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True,
-                           W.W2(phi).seed) for phi in W.W2_POROSITIES]
+        cases = [W.W2_half(phi) for phi in W.W2_POROSITIES]
     elif args.workload == "large":   # one 512x512x1024 channel (W2's structure, porosity 0.6)
         cases = [W.W3_LARGE]
+    elif args.workload == "w0":   # the paper's single-sphere block: 151^3 periodic, one sphere D = 90
+        cases = [W.W0]
     else:   # rev: the periodic REV cubes as one batch
         cases = [W.W4_cube(i) for i in range(args.cubes)]
-    geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
+    if args.workload == "w0":
+        geoms = [L.lbm_geometry_from_list(*W.W0_BOX, True, W.W0_SPHERES)]
+    else:
+        geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
     c0 = cases[0]
     if args.workload == "rev":
         solvers = [L.BatchSolver(geoms, c0.tau, c0.lam, c0.g, args.storage, flags=odd_flags(args))]
@@ -492,14 +521,16 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--odd", choices=["auto", "table", "rows"], default="auto",
                     help="neighbour indices of the odd step (library default, int32 table, row bitmasks)")
+    ap.add_argument("--bounce-back", action="store_true",
+                    help="simple bounce-back on every wall link instead of CLI (Eq. (noslip), q = 1/2 forced)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
-    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "rev", "surrogate", "unet"],
+    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet"],
                     default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "

@@ -109,6 +109,11 @@ typedef struct {
  * steps in chunks as a CUDA graph.  These flags turn either off. */
 #define LBM_FLAG_NO_GRAPH 4
 #define LBM_FLAG_NO_AUTOTUNE 8
+/* Simple bounce-back (Eq. (noslip): every wall surface half-way along its
+ * link, q = 1/2 forced) on every wall link instead of Eq. (CLI).  The link
+ * fractions q are still computed and exported; every link reports the
+ * bounce-back fallback. */
+#define LBM_FLAG_SIMPLE_BOUNCE_BACK 32
 
 /* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
  * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes

@@ -34,6 +34,7 @@ LBM_FLAG_NEIGHBOUR_TABLE = 1
 LBM_FLAG_ROW_NEIGHBOURS = 2
 LBM_FLAG_NO_GRAPH = 4
 LBM_FLAG_NO_AUTOTUNE = 8
+LBM_FLAG_SIMPLE_BOUNCE_BACK = 32
 
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1

@@ -102,7 +102,8 @@ static bool params_ok(const lbm_params *p)
     if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return false;
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return false;
-    const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE;
+    const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE |
+                          LBM_FLAG_SIMPLE_BOUNCE_BACK;
     if ((p->flags & ~known) != 0) return false;
     if ((p->flags & LBM_FLAG_NEIGHBOUR_TABLE) && (p->flags & LBM_FLAG_ROW_NEIGHBOURS)) return false;
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
@@ -639,7 +640,8 @@ int lbm_export_lists(lbm_solver *s, int32_t *fluid_cell, int32_t *nbr, int32_t *
                     if (link_cell) link_cell[l] = (int32_t)i;
                     if (link_k) link_k[l] = (int8_t)k;
                     if (link_fallback) {
-                        bool fb = ((mask[i] >> opp(k)) & 1u) || qs[l] < kCliQmin;
+                        bool fb = (s->params.flags & LBM_FLAG_SIMPLE_BOUNCE_BACK) || ((mask[i] >> opp(k)) & 1u) ||
+                                  qs[l] < kCliQmin;
                         if (!fb) fb = (mask[nb[(size_t)(opp(k) - 1) * nf + i]] >> opp(k)) & 1u;
                         link_fallback[l] = (uint8_t)fb;
                     }

@@ -197,6 +197,7 @@ struct LinkArgs {
     int nx, ny, nz, periodic_z;
     int nbx, nby;
     double q_lo, q_hi;
+    int simple_bounce_back;   // every link a = 0 (LBM_FLAG_SIMPLE_BOUNCE_BACK)
 };
 
 // 5. link fractions and CLI coefficients of the cells of one part.  The grid
@@ -243,7 +244,7 @@ __global__ void k_links(LinkArgs a)
         // wall node on the link's line (x - 2 e_k solid), or when the wall is
         // within kCliQmin of the node: Eq. (CLI) grows without bound in such
         // sharp corners of overlapping packings
-        bool fallback = ((m >> opp(k)) & 1u) || q < kCliQmin;
+        bool fallback = a.simple_bounce_back || ((m >> opp(k)) & 1u) || q < kCliQmin;
         if (!fallback) {
             const int32_t x2 = a.nbr[(size_t)(opp(k) - 1) * a.n_pad + i];
             fallback = (a.lmask[x2] >> opp(k)) & 1u;
@@ -346,7 +347,7 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
         const int32_t begin = P.fluid_off, end = P.fluid_off + P.n_fluid;
         LinkArgs la{s.fluid_cell, s.nbr, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, begin, end,
                     s.n_fluid, s.n_pad, P.cell_base, P.box.nx, P.box.ny, P.box.nz, P.box.periodic_z, bins.nbx,
-                    bins.nby, P.box.q_lo, P.box.q_hi};
+                    bins.nby, P.box.q_lo, P.box.q_hi, (s.params.flags & LBM_FLAG_SIMPLE_BOUNCE_BACK) ? 1 : 0};
         k_links<<<blocks_for(end - (begin & ~31)), kBlock, 0, st>>>(la);
         LBM_CUDA_TRY(cudaGetLastError());
         // the host bins must outlive their (pageable, staged) copies: synchronise

@@ -77,10 +77,21 @@ def W4_cube(i: int) -> Channel:
                    4000 + i, periodic_z=True)
 
 
+def W2_half(phi: float) -> Channel:
+    """The W2 channel at half the size (128x128x256, porous layer z < 128,
+    same radius and seeds), for profiler captures and converged profiles;
+    permeability window z in [17, 112)."""
+    return Channel(f"half-size channel phi={phi}", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, phi, True, W2(phi).seed,
+                   perm_window=(17, 112))
+
+
 # The paper's weak-scaling block: 151^3 periodic cube, one centred sphere of
 # diameter 90 (explicit list).
 W0_BOX = (151, 151, 151)
 W0_SPHERES = np.array([[75.0, 75.0, 75.0, 45.0]])
+# its flow parameters (the sphere comes from W0_SPHERES, not from placement)
+W0 = Channel("W0 151^3 periodic, one sphere D=90", 151, 151, 151, 0.0, 151.0, 45.0, 45.0, 0.0, False, 0,
+             periodic_z=True)
 
 
 def small_cases():

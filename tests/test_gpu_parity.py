@@ -297,3 +297,34 @@ def test_odd_step_variants_agree(torch_cuda, flags):
     b.step(9)
     pa, pb = a.populations(), b.populations()
     assert float((pa - pb).abs().max()) <= 1e-6 * float(pb.abs().max())
+
+
+@pytest.mark.parametrize("variant", ["simple bounce-back", "SRT", "Lambda 1/4"])
+def test_boundary_and_collision_variants(torch_cuda, variant):
+    """Forced simple bounce-back (Eq. (noslip) on every link), SRT (TRT with
+    Lambda = (tau - 1/2)^2) and Lambda = 1/4 on a sphere packing with off-grid
+    walls: every population after 10 steps against the oracle."""
+    torch = torch_cuda
+    case = CASES[3]
+    tau, lam, flags, sbb = case.tau, case.lam, 0, False
+    if variant == "simple bounce-back":
+        flags, sbb = L.LBM_FLAG_SIMPLE_BOUNCE_BACK, True
+    elif variant == "SRT":
+        tau = 1.1
+        lam = (tau - 0.5) ** 2
+    else:
+        lam = 0.25
+    g = (3e-5, -1e-5, 2e-5)
+    u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=21, amplitude=2e-2)
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args(), q_lo=case.q_lo, q_hi=case.q_hi)
+    solver = L.Solver(geom, tau, lam, g, u0=torch.from_numpy(u0).cuda(), flags=flags)
+    lat = O.Lattice(case.nx, case.ny, case.nz, case.periodic_z, geom.spheres(), tau, lam, g, case.q_lo, case.q_hi,
+                    simple_bounce_back=sbb).init(u0.astype(np.float64))
+    solver.step(10)
+    lat.step(10)
+    lists = solver.export_lists()
+    got = solver.populations().cpu().numpy().astype(np.float64)
+    want = _oracle_shifted(lat, lists["fluid_cell"])
+    assert np.max(np.abs(got - want)) <= TOL_U * np.max(np.abs(want))
+    if sbb:
+        assert lists["link_fallback"].all()
