@@ -317,6 +317,58 @@ def run_unet(args):
     print(json.dumps(line), flush=True)
 
 
+def run_glbm(args):
+    """Steps of the homogenised porous-medium LBM (Sec. 4) on a dense
+    256x256x512 box: walls z = 0/511, lower half a porous layer (eps = 0.6,
+    K = 1, nu_eff = nu / eps), body force 1e-6; MLUPS over the fluid cells
+    and the roofline of the 152 B/FLUP algorithmic traffic."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    nx, ny, nz, nu = 256, 256, 512, 0.1
+    z = np.arange(nz)
+    porous = (z >= 1) & (z < nz // 2)
+    eps = np.where(porous, 0.6, 1.0)
+    inv_k = np.where(porous, 1.0, 0.0)
+    solver = L.GLBM(nx, ny, nz, eps, inv_k, 3 * nu / eps + 0.5, nu, 0.0, (1e-6, 0.0, 0.0))
+    stream = torch.cuda.current_stream()
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        solver.step(1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    durs = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)])
+    ms = float(durs.sum())
+    nf = solver.n_fluid
+    peak, peak_kind = _peak_hbm()
+    first_parity = args.warmup & 1
+    parity = {("even" if (first_parity + off) % 2 == 0 else "odd"): float(nf * 152 / (durs[off::2].mean() * 1e-3) / 1e9)
+              for off in (0, 1) if durs[off::2].size}
+    achieved = float(nf * 152 / (durs.mean() * 1e-3) / 1e9)
+    line = {"metric": "fluid MLUPS of the homogenised porous-medium LBM (Sec. 4, Guo & Zhao GLBM)",
+            "value": nf * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"dense {nx}x{ny}x{nz} box, walls z=0/{nz - 1}, porous lower half eps=0.6 K=1, "
+                                   "nu_eff=nu/eps, G=1e-6", "fluid_cells": nf},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_flup": 152, "peak_kind": peak_kind, "by_parity": parity,
+                         "kernel": "k_glbm_even/k_glbm_odd"},
+            "clocks": clk, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """Time to steady state with and without the learned warm start: solver-
     generated training data, training with the library's U-Net kernels, and
@@ -530,11 +582,11 @@ def main():
                     help="simple bounce-back on every wall link instead of CLI (Eq. (noslip), q = 1/2 forced)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
-    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet"],
+    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet", "glbm"],
                     default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
-                         "warm versus cold start; unet: U-Net training steps")
+                         "warm versus cold start; unet: U-Net training steps; glbm: the homogenised model")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
@@ -554,6 +606,8 @@ def main():
         run_surrogate(args)
     elif args.workload == "unet":
         run_unet(args)
+    elif args.workload == "glbm":
+        run_glbm(args)
     elif args.converge:
         run_converge(args)
     else:

@@ -68,6 +68,12 @@ class lbm_params(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+class glbm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("periodic_z", ctypes.c_int32), ("nu", ctypes.c_double), ("c_f", ctypes.c_double),
+                ("g", ctypes.c_double * 3), ("u_bottom", ctypes.c_double * 3), ("u_top", ctypes.c_double * 3)]
+
+
 class lbm_geometry_info(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("n_fluid", ctypes.c_int64), ("n_links", ctypes.c_int64),
                 ("n_spheres", ctypes.c_int64), ("porosity", ctypes.c_double)]
@@ -114,6 +120,15 @@ SIGNATURES = {
     "lbm_batch_profile_residual": (_I, [_P, _P]),
     "lbm_schedule": (_I, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                           ctypes.POINTER(_I32)]),
+    # include/glbm.h
+    "glbm_workspace_size": (_I, [ctypes.POINTER(glbm_params), ctypes.POINTER(_SZ)]),
+    "glbm_init": (_I, [ctypes.POINTER(glbm_params), _P, _P, _P, _P, _SZ, _P, _P, ctypes.POINTER(_P)]),
+    "glbm_step": (_I, [_P, _I64]),
+    "glbm_moments": (_I, [_P, _P, _P]),
+    "glbm_plane_average": (_I, [_P, _P]),
+    "glbm_populations": (_I, [_P, _P]),
+    "glbm_steps_done": (_I, [_P, ctypes.POINTER(_I64)]),
+    "glbm_destroy": (None, [_P]),
     # include/unet.h
     "lbm_sdf_workspace_size": (_I, [_P, ctypes.c_float, ctypes.POINTER(_SZ)]),
     "lbm_sdf": (_I, [_P, ctypes.c_float, _P, _SZ, _P, _P]),
@@ -475,6 +490,70 @@ def lbm_sdf(geom: Geometry, trunc: float = 8.0, out=None, stream=None):
     _check(load_library().lbm_sdf(geom.handle, float(trunc), _dev_ptr(ws), ws.numel(), _dev_ptr(out),
                                   ctypes.c_void_p(stream)), "lbm_sdf")
     return out
+
+
+class GLBM:
+    """The homogenised porous-medium LBM (include/glbm.h) with its device
+    workspace.  eps, inv_k (1/K) and tau are per z-plane (length nz or
+    scalars)."""
+
+    def __init__(self, nx, ny, nz, eps, inv_k, tau, nu, c_f=0.0, g=(0.0, 0.0, 0.0), u_bottom=(0.0, 0.0, 0.0),
+                 u_top=(0.0, 0.0, 0.0), periodic_z=False, u0=None, stream=None):
+        import torch
+
+        lib = load_library()
+        p = glbm_params(int(nx), int(ny), int(nz), int(bool(periodic_z)), float(nu), float(c_f),
+                        (ctypes.c_double * 3)(*g), (ctypes.c_double * 3)(*u_bottom), (ctypes.c_double * 3)(*u_top))
+        self.shape = (int(nz), int(ny), int(nx))
+        col = lambda a: np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64).reshape(-1), (nz,)))
+        e, ik, t = col(eps), col(inv_k), col(tau)
+        ws = _SZ()
+        _check(lib.glbm_workspace_size(ctypes.byref(p), ctypes.byref(ws)), "glbm_workspace_size")
+        self.workspace = torch.empty(int(ws.value), dtype=torch.uint8, device="cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = _P()
+        _check(lib.glbm_init(ctypes.byref(p), _np_ptr(e), _np_ptr(ik), _np_ptr(t), _dev_ptr(self.workspace),
+                             self.workspace.numel(), _dev_ptr(u0) if u0 is not None else None,
+                             ctypes.c_void_p(stream), ctypes.byref(h)), "glbm_init")
+        self._h = h
+        self.n_fluid = int(nx) * int(ny) * (int(nz) if periodic_z else int(nz) - 2)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            load_library().glbm_destroy(self._h)
+            self._h = None
+
+    def step(self, n: int = 1):
+        _check(load_library().glbm_step(self._h, int(n)), "glbm_step")
+        return self
+
+    @property
+    def steps(self) -> int:
+        v = _I64()
+        _check(load_library().glbm_steps_done(self._h, ctypes.byref(v)), "glbm_steps_done")
+        return v.value
+
+    def moments(self):
+        import torch
+
+        rho = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        u = torch.empty((3,) + self.shape, dtype=torch.float32, device="cuda")
+        _check(load_library().glbm_moments(self._h, _dev_ptr(rho), _dev_ptr(u)), "glbm_moments")
+        return rho, u
+
+    def plane_average(self) -> np.ndarray:
+        out = np.zeros(self.shape[0], np.float64)
+        _check(load_library().glbm_plane_average(self._h, _np_ptr(out)), "glbm_plane_average")
+        return out
+
+    def populations(self):
+        """f_k - w_k of the current time, [19, n_fluid] float32 on the device."""
+        import torch
+
+        out = torch.empty((19, self.n_fluid), dtype=torch.float32, device="cuda")
+        _check(load_library().glbm_populations(self._h, _dev_ptr(out)), "glbm_populations")
+        return out
 
 
 class UNet:

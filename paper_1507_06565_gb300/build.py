@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "liblbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["lbm_geometry.cpp", "lbm_api.cpp", "lbm_build.cu", "lbm_step.cu", "lbm_post.cu", "lbm_static_scratch.cu",
-           "lbm_sdf.cu", "unet.cu"]
+           "lbm_sdf.cu", "unet.cu", "glbm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -49,7 +49,8 @@ def _stale(objs: list[str]) -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "lbm.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    deps.append(__file__)
     return any(os.path.getmtime(d) > t for d in deps)
 
 

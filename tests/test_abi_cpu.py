@@ -1,5 +1,5 @@
 """CPU-side checks of the C-ABI library: it builds, loads and exports every
-symbol of include/lbm.h, and its host geometry (sphere placement, voxel mask)
+symbol of include/*.h, and its host geometry (sphere placement, voxel mask)
 equals the oracle's bit for bit.  No GPU kernel is launched here."""
 import os
 import re
@@ -27,7 +27,7 @@ def _declared_symbols():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"\b((?:lbm|unet)_[a-z0-9_]+)\s*\(", src))
+            names |= set(re.findall(r"\b((?:lbm|unet|glbm)_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
 
