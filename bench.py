@@ -369,6 +369,69 @@ def run_glbm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_homogenised(args):
+    """Sec. 4's comparison on synthetic data: the pore-scale channel (half-size
+    W2 shape, porosity 0.6) run to a steady profile; its plane porosity
+    eps(z) and permeability K_b (porous window) drive the homogenised LBM
+    on the same channel, with K(z) = K_b * CK(eps(z)) / CK(eps_b) (Carman-Kozeny
+    scaling, CK(e) = e^3 / (1 - e)^2, eps_b the mean porosity of the window;
+    K = infinity where eps = 1), Stokes regime (no Forchheimer term), run to
+    steady state with nu_eff = nu (standard GLBM) and nu_eff = nu / eps (the
+    paper's proposal).  Reports the deviation of each homogenised profile
+    from the plane-averaged pore-scale one."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    case = W.W2_half(0.6)
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+    dns = L.Solver(geom, case.tau, case.lam, case.g)
+    t0 = time.perf_counter()
+    rc, n_dns, res = dns.run_until(args.tol, args.interval, args.max_steps, criterion="profile")
+    torch.cuda.synchronize()
+    t_dns = time.perf_counter() - t0
+    pa = dns.plane_average()
+    u_dns, eps = pa[:, 0], pa[:, 2]
+    k_b = dns.permeability(*case.perm_window)
+    z0, z1 = case.perm_window
+    eps_b = float(eps[z0:z1].mean())
+    ck = lambda e: e ** 3 / np.maximum(1.0 - e, 1e-12) ** 2
+    nz = case.nz
+    eps_h = np.where(eps > 0, np.clip(eps, 1e-3, 1.0), 1.0)
+    eps_h[0] = eps_h[-1] = 1.0
+    inv_k = np.where(eps_h < 1.0 - 1e-9, ck(eps_b) / (k_b * ck(eps_h)), 0.0)
+    nu = (case.tau - 0.5) / 3.0
+    fluid = slice(1, nz - 1)
+    out = {}
+    for name, tau in (("nu_eff = nu", np.full(nz, case.tau)), ("nu_eff = nu / eps", 3.0 * nu / eps_h + 0.5)):
+        h = L.GLBM(4, 4, nz, eps_h, inv_k, tau, nu, 0.0, case.g)
+        prev, steps = None, 0
+        while steps < 2_000_000:
+            h.step(20_000)
+            steps += 20_000
+            prof = h.plane_average()
+            if prev is not None and np.linalg.norm(prof - prev) <= 1e-8 * np.linalg.norm(prof):
+                break
+            prev = prof
+        dev = np.abs(prof[fluid] - u_dns[fluid])
+        ref = np.max(np.abs(u_dns[fluid]))
+        out[name] = {"steps": steps, "max_dev_rel": float(dev.max() / ref),
+                     "l2_dev_rel": float(np.linalg.norm(prof[fluid] - u_dns[fluid]) / np.linalg.norm(u_dns[fluid])),
+                     "porous_max_dev_rel": float(dev[: z1 - 1].max() / ref),
+                     "u_every8": prof[::8].tolist()}
+    line = {"metric": "homogenised vs pore-scale plane-averaged velocity (Sec. 4)", "unit": "relative deviation",
+            "value": out["nu_eff = nu / eps"]["l2_dev_rel"], "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"{case.name}: pore-scale to profile residual {args.tol:g}, then GLBM with its "
+                                   "plane porosity and permeability"},
+            "dns": {"status": L.status_string(rc), "steps": n_dns, "seconds": t_dns, "permeability": k_b,
+                    "eps_bulk": eps_b, "u_every8": u_dns[::8].tolist(), "eps_every8": eps[::8].tolist()},
+            "homogenised": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """Time to steady state with and without the learned warm start: solver-
     generated training data, training with the library's U-Net kernels, and
@@ -582,11 +645,13 @@ def main():
                     help="simple bounce-back on every wall link instead of CLI (Eq. (noslip), q = 1/2 forced)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
-    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet", "glbm"],
+    ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet", "glbm",
+                                           "homogenised"],
                     default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
-                         "warm versus cold start; unet: U-Net training steps; glbm: the homogenised model")
+                         "warm versus cold start; unet: U-Net training steps; glbm: the homogenised model; "
+                         "homogenised: the homogenised model against the pore-scale profile")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
@@ -608,6 +673,8 @@ def main():
         run_unet(args)
     elif args.workload == "glbm":
         run_glbm(args)
+    elif args.workload == "homogenised":
+        run_homogenised(args)
     elif args.converge:
         run_converge(args)
     else:
