@@ -422,13 +422,28 @@ def run_homogenised(args):
                      "l2_dev_rel": float(np.linalg.norm(prof[fluid] - u_dns[fluid]) / np.linalg.norm(u_dns[fluid])),
                      "porous_max_dev_rel": float(dev[: z1 - 1].max() / ref),
                      "u_every8": prof[::8].tolist()}
+    # two-domain interface parameters from the pore-scale profile (Sec. 3.2),
+    # at the first all-fluid plane and two planes below it
+    from paper_1507_06565_gb300 import interface as I
+
+    zc = np.arange(nz, dtype=float)
+    z_top = nz - 1.5
+    fits = {}
+    zi0 = I.interface_position(zc[1:-1], eps[1:-1])
+    for zi in (zi0, zi0 - 2.0):
+        try:
+            f = I.fit_interface(zc[1:-1], u_dns[1:-1], zi, k_b, nu, nu_eff=nu / eps_b)
+            fits[f"z_int={zi:g}"] = {"u_s": f.u_s, "du_free": f.du_free, "du_porous": f.du_porous, "u_m": f.u_m,
+                                     "alpha_bj": f.alpha_bj, "alpha_bjs": f.alpha_bjs, "beta_otw": f.beta_otw}
+        except ValueError as exc:
+            fits[f"z_int={zi:g}"] = {"error": str(exc)}
     line = {"metric": "homogenised vs pore-scale plane-averaged velocity (Sec. 4)", "unit": "relative deviation",
             "value": out["nu_eff = nu / eps"]["l2_dev_rel"], "higher_is_better": False, "data": "synthetic",
             "config": {"workload": f"{case.name}: pore-scale to profile residual {args.tol:g}, then GLBM with its "
                                    "plane porosity and permeability"},
             "dns": {"status": L.status_string(rc), "steps": n_dns, "seconds": t_dns, "permeability": k_b,
                     "eps_bulk": eps_b, "u_every8": u_dns[::8].tolist(), "eps_every8": eps[::8].tolist()},
-            "homogenised": out}
+            "homogenised": out, "interface": fits, "z_top_wall": z_top}
     print(json.dumps(line), flush=True)
 
 
