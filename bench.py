@@ -447,6 +447,93 @@ def run_homogenised(args):
     print(json.dumps(line), flush=True)
 
 
+# force of the coarsest study case: a free layer of ~15 cells with nu = 0.1
+# peaks near g L^2 / (8 nu) = 0.05, i.e. Re_D = u_max D / nu ~ 2 at D = 4
+STUDY_G1 = 1.8e-4
+
+
+def _study_case(scale, g, tol, interval, max_steps):
+    """One pore-scale channel of the resolution study: the seeded packing of
+    a 16x16x32 channel (walls z = 0/31, overlapping spheres of diameter 4 in
+    z < 16, porosity 0.6), every length scaled by `scale` (sphere centres
+    about the bottom wall surface z = 1/2, radii, box); run to the profile
+    tolerance.  Returns (normalised height, u / u_max, steps, u_max, Re_D)."""
+    import paper_1507_06565_gb300 as L
+
+    base = W.Channel("study base", 16, 16, 32, 1.0, 16.0, 2.0, 2.0, 0.6, True, 2060)
+    sp = L.lbm_geometry_from_spheres(*base.sphere_args()).spheres()
+    sc = sp.copy()
+    sc[:, 0] *= scale
+    sc[:, 1] *= scale
+    sc[:, 2] = 0.5 + scale * (sp[:, 2] - 0.5)
+    sc[:, 3] *= scale
+    nx, nz = 16 * scale, 30 * scale + 2
+    geom = L.lbm_geometry_from_list(nx, nx, nz, False, sc)
+    solver = L.Solver(geom, base.tau, base.lam, (g, 0.0, 0.0))
+    rc, n, _ = solver.run_until(tol, interval, max_steps, criterion="profile")
+    u = solver.plane_average()[1:-1, 0]
+    h = (np.arange(1, nz - 1) - 0.5) / (nz - 2)
+    nu = (base.tau - 0.5) / 3.0
+    return h, u / u.max(), n, float(u.max()), float(u.max() * 4 * scale / nu), L.status_string(rc)
+
+
+def run_grid_study(args):
+    """Grid study of the pore-scale profile (Sec. 3.1): the same packing at
+    sphere diameters D = 4, 8, 16, 32 lattice units, the force scaled as
+    1/scale^3 to keep Re_D = u_max D / nu near 2; the normalised profiles
+    are compared on the coarsest heights."""
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    runs, prof = [], {}
+    g1 = STUDY_G1
+    for scale in (1, 2, 4, 8):
+        t0 = time.perf_counter()
+        h, un, n, umax, re, st = _study_case(scale, g1 / scale ** 3, args.tol, args.interval, args.max_steps)
+        prof[scale] = (h, un)
+        runs.append({"D": 4 * scale, "steps": n, "status": st, "u_max": umax, "Re_D": re,
+                     "seconds": time.perf_counter() - t0})
+    h1 = prof[1][0]
+    diffs = {}
+    for a, b in ((1, 2), (2, 4), (4, 8)):
+        ua = np.interp(h1, *prof[a])
+        ub = np.interp(h1, *prof[b])
+        diffs[f"D{4 * a}-D{4 * b}"] = float(np.linalg.norm(ua - ub) / np.linalg.norm(ub))
+    line = {"metric": "pore-scale profile change between resolutions (u/u_max on z/H)", "unit": "relative L2",
+            "value": diffs["D16-D32"], "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "16x16x32 channel packing (overlapping D=4 spheres, porosity 0.6, lower half) "
+                                   "scaled x1, x2, x4, x8; Re_D ~ 2", "tol": args.tol},
+            "runs": runs, "profile_change": diffs,
+            "profiles_every_coarse_plane": {f"D{4 * k}": np.interp(h1, *v).tolist() for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+
+
+def run_re_sweep(args):
+    """Reynolds-number sweep of the pore-scale profile (Sec. 3.1): the D = 16
+    packing of the grid study, the force scaled to Re_D ~ 0.2 .. 16 (viscosity
+    and geometry fixed); reports where the normalised profile peaks and how
+    much flow enters the porous half."""
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    runs = []
+    for factor in (0.1, 1.0, 3.0, 8.0):
+        h, un, n, umax, re, st = _study_case(4, factor * STUDY_G1 / 64, args.tol, args.interval, args.max_steps)
+        runs.append({"force_factor": factor, "Re_D": re, "u_max": umax, "steps": n, "status": st,
+                     "z_max_over_H": float(h[int(np.argmax(un))]),
+                     "porous_half_mean_u_over_max": float(un[h < 0.5].mean()),
+                     "profile_every4": un[::4].tolist()})
+    line = {"metric": "pore-scale profile vs Re_D (peak height and porous-layer flow)", "unit": "z/H",
+            "value": runs[-1]["z_max_over_H"], "higher_is_better": None, "data": "synthetic",
+            "config": {"workload": "64x64x122 channel (D=16 packing of the grid study)", "tol": args.tol},
+            "runs": runs}
+    print(json.dumps(line), flush=True)
+
+
 def run_surrogate(args):
     """Time to steady state with and without the learned warm start: solver-
     generated training data, training with the library's U-Net kernels, and
@@ -661,12 +748,13 @@ def main():
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
     ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet", "glbm",
-                                           "homogenised"],
+                                           "homogenised", "grid-study", "re-sweep"],
                     default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
                          "warm versus cold start; unet: U-Net training steps; glbm: the homogenised model; "
-                         "homogenised: the homogenised model against the pore-scale profile")
+                         "homogenised: the homogenised model against the pore-scale profile; grid-study, "
+                         "re-sweep: the resolution and Reynolds-number studies of the pore-scale profile")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
@@ -690,6 +778,10 @@ def main():
         run_glbm(args)
     elif args.workload == "homogenised":
         run_homogenised(args)
+    elif args.workload == "grid-study":
+        run_grid_study(args)
+    elif args.workload == "re-sweep":
+        run_re_sweep(args)
     elif args.converge:
         run_converge(args)
     else:
