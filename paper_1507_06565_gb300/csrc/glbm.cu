@@ -117,7 +117,9 @@ __device__ __forceinline__ void macro(const float h[kQ], const Plane &P, const A
     for (int d = 0; d < 3; ++d) F[d] = -(P.drag1 + P.drag2 * un) * u[d] + P.eps * a.g[d];
 }
 
-// BGK collision with Guo & Zhao's equilibrium and source, in place on h.
+// BGK collision with Guo & Zhao's equilibrium and source, in place on h,
+// over opposite pairs (k, k+1): e_{k+1} = -e_k, so the pair shares w, e.u and
+// e.F up to sign, which keeps few values live.
 __device__ __forceinline__ float collide(float h[kQ], const Plane &P, const Args &a)
 {
     float drho, u[3], F[3];
@@ -125,14 +127,26 @@ __device__ __forceinline__ float collide(float h[kQ], const Plane &P, const Args
     const float rho = 1.0f + drho;
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const float rs = rho * P.src;
+    // rest population: e = 0
+    {
+        const float w = (float)weight(0);
+        const float heq = w * (drho - rho * 1.5f * uu * P.inv_eps);
+        h[0] = h[0] - P.omega * (h[0] - heq) - w * rs * 3.0f * uF * P.inv_eps;
+    }
 #pragma unroll
-    for (int k = 0; k < kQ; ++k) {
+    for (int k = 1; k < kQ; k += 2) {
         const float w = (float)weight(k);
         const float eu = ex(k) * u[0] + ey(k) * u[1] + ez(k) * u[2];
         const float eF = ex(k) * F[0] + ey(k) * F[1] + ez(k) * F[2];
-        const float heq = w * (drho + rho * (3.0f * eu + (4.5f * eu * eu - 1.5f * uu) * P.inv_eps));
-        const float sk = w * rho * P.src * (3.0f * eF + (9.0f * eu * eF - 3.0f * uF) * P.inv_eps);
-        h[k] = h[k] - P.omega * (h[k] - heq) + sk;
+        // symmetric and antisymmetric parts of the pair's equilibrium and source
+        const float eq_s = w * (drho + rho * (4.5f * eu * eu - 1.5f * uu) * P.inv_eps);
+        const float eq_a = w * rho * 3.0f * eu;
+        const float src_s = w * rs * (9.0f * eu * eF - 3.0f * uF) * P.inv_eps;
+        const float src_a = w * rs * 3.0f * eF;
+        const float hk = h[k], hb = h[k + 1];
+        h[k] = hk - P.omega * (hk - (eq_s + eq_a)) + src_s + src_a;
+        h[k + 1] = hb - P.omega * (hb - (eq_s - eq_a)) + src_s - src_a;
     }
     return rho;
 }
@@ -149,39 +163,44 @@ __global__ void __launch_bounds__(kBlock, 3) k_glbm_even(Args a)
 {
     const int32_t c = blockIdx.x * kBlock + threadIdx.x;
     if (c >= a.n_cells) return;
-    int z;
-    const Offsets o = offsets(a, c, z);
-    const Plane P = a.planes[z];
     const uint32_t n_pad = (uint32_t)a.n_pad;
     float h[kQ];
 #pragma unroll
     for (int k = 0; k < kQ; ++k) h[k] = a.pdf[k * n_pad + (uint32_t)c];
-    const float rho = collide(h, P, a);
+    const int zf = c / (a.nx * a.ny);
+    const float rho = collide(h, a.planes[a.z0 + zf], a);
+    // f~_k goes to slot opp(k) of this cell
 #pragma unroll
-    for (int k = 0; k < kQ; ++k) {
-        // f~_k goes to slot opp(k) of this cell (the dead slot for a wall link)
-        float v = h[k];
-        if (ez(k) && o.oz[ez(k) + 1] == kWall) v = bounced(a, k, v, rho);
-        a.pdf[opp(k) * n_pad + (uint32_t)c] = v;
+    for (int k = 0; k < kQ; ++k) a.pdf[opp(k) * n_pad + (uint32_t)c] = h[k];
+    // next to a wall plane that slot is the dead slot of the link: it holds
+    // the bounced population instead (a second store, on two planes only)
+    const int side = a.periodic_z ? 0 : (zf == 0 ? -1 : (zf == a.nzf - 1 ? 1 : 0));
+    if (side) {
+#pragma unroll
+        for (int k = 1; k < kQ; ++k)
+            if (ez(k) == side) a.pdf[opp(k) * n_pad + (uint32_t)c] = bounced(a, k, h[k], rho);
     }
 }
 
-__global__ void __launch_bounds__(kBlock, 3) k_glbm_odd(Args a)
+__global__ void __launch_bounds__(kBlock, 4) k_glbm_odd(Args a)
 {
     const int32_t c = blockIdx.x * kBlock + threadIdx.x;
     if (c >= a.n_cells) return;
     int z;
-    const Offsets o = offsets(a, c, z);
-    const Plane P = a.planes[z];
     const uint32_t n_pad = (uint32_t)a.n_pad;
     float h[kQ];
-    h[0] = a.pdf[(uint32_t)c];
+    {
+        const Offsets o = offsets(a, c, z);
+        h[0] = a.pdf[(uint32_t)c];
 #pragma unroll
-    for (int k = 1; k < kQ; ++k) {
-        const int32_t up = nb(o, c, k, -1);
-        h[k] = up >= 0 ? a.pdf[opp(k) * n_pad + (uint32_t)up] : a.pdf[k * n_pad + (uint32_t)c];
+        for (int k = 1; k < kQ; ++k) {
+            const int32_t up = nb(o, c, k, -1);
+            h[k] = up >= 0 ? a.pdf[opp(k) * n_pad + (uint32_t)up] : a.pdf[k * n_pad + (uint32_t)c];
+        }
     }
-    const float rho = collide(h, P, a);
+    const float rho = collide(h, a.planes[z], a);
+    // the offsets again (cheaper than keeping them live across the collision)
+    const Offsets o = offsets(a, c, z);
     a.pdf[(uint32_t)c] = h[0];
 #pragma unroll
     for (int k = 1; k < kQ; ++k) {
