@@ -35,9 +35,10 @@ METRIC = "fluid MLUPS (D3Q19 TRT + CLI stream-collide; HBM roofline fraction in 
 WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlapping r=8 spheres, "
             "porosity sweep {0.4,0.6,0.8,0.9} (one solver each); one step = one time step of all four")
 # measured DRAM read + write bytes per fluid cell of one launch (FP32 storage,
-# neighbour table): ncu on the default command, full-grid launches of all four
-# solvers (see profiles/step_kernels_channel_256x256x512_dram.txt)
-MEASURED_DRAM_B_PER_FLUP = {"even": 155.2, "odd": 223.5}
+# neighbour table outside the dense tiles): ncu on the default command,
+# full-grid launches of all four solvers (see
+# profiles/step_kernels_channel_256x256x512_dram.txt)
+MEASURED_DRAM_B_PER_FLUP = {"even": 155.2, "odd": 181.3}
 # bounded samples of the workload for the CPU oracle: same sphere radius,
 # porosity and channel structure at a reduced box
 SAMPLE = W.Channel("W2-shaped sample 128x128x256 r=8 phi=0.6", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, 0.6, True, 2060)

@@ -52,6 +52,7 @@ Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size
     L.link_q = take((size_t)(n_links > 0 ? n_links : 1) * 8);
     L.fluid_cell = take((size_t)n_pad * 4);
     L.plane_off = take((size_t)n_poff * 4);
+    L.tile_desc = take((size_t)n_pad / kBlock * 8);
     L.row_words = take(single ? (size_t)b0.ny * b0.nz * ((b0.nx + 31) / 32) * 8 : 0);
     L.cell_xr = take(single ? (size_t)n_pad * 4 : 0);
     L.u_cur = take((size_t)3 * n_pad * 4);
@@ -205,6 +206,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->plane_off = (int32_t *)(s->ws + L.plane_off);
     s->row_words = (uint2 *)(s->ws + L.row_words);
     s->cell_xr = (uint32_t *)(s->ws + L.cell_xr);
+    s->tile_desc = (int2 *)(s->ws + L.tile_desc);
     s->u_cur = (float *)(s->ws + L.u_cur);
     s->u_prev = (float *)(s->ws + L.u_prev);
     s->rho_cur = (float *)(s->ws + L.rho_cur);

@@ -269,6 +269,27 @@ __global__ void k_plane_offsets(const int32_t *__restrict__ fluid_cell, int32_t 
         for (int zz = z + 1; zz <= nz; ++zz) plane_off[zz] = end;
 }
 
+// Dense tiles of one part (see Solver::tile_desc): tile t holds fluid cells
+// t*kBlock .. t*kBlock+kBlock-1; it is dense when they all belong to this part
+// and lie in planes z with 1 <= z <= nz - 2 such that planes z - 1, z, z + 1
+// are fully fluid.  One thread per tile of the part.
+__global__ void k_dense_tiles(const int32_t *__restrict__ fluid_cell, const int32_t *__restrict__ plane_off,
+                              int32_t begin, int32_t end, int64_t cell_base, int nx, int ny, int nz,
+                              int2 *__restrict__ desc)
+{
+    const int32_t t = begin / kBlock + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int32_t first = t * kBlock, last = first + kBlock - 1;
+    if (first >= end) return;
+    if (first < begin || last >= end) return;   // straddles a part boundary or the end: not dense
+    const int64_t plane = (int64_t)nx * ny;
+    const int z0 = (int)((fluid_cell[first] - cell_base) / plane);
+    const int z1 = (int)((fluid_cell[last] - cell_base) / plane);
+    if (z0 < 1 || z1 > nz - 2) return;
+    for (int z = z0 - 1; z <= z1 + 1; ++z)
+        if ((int64_t)(plane_off[z + 1] - plane_off[z]) != plane) return;
+    desc[t] = make_int2(plane_off[z0], nx | (ny << 16));
+}
+
 }  // namespace
 
 #define LBM_CUDA_TRY(x)                                     \
@@ -293,6 +314,7 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     uint32_t *cell_xr = single ? s.cell_xr : nullptr;
     std::vector<uint32_t> counts(s.parts.size() + 1, 0);
 
+    LBM_CUDA_TRY(cudaMemsetAsync(s.tile_desc, 0xFF, sizeof(int2) * (s.n_pad / kBlock), st));
     for (size_t b = 0; b < s.parts.size(); ++b) {
         const Part &P = s.parts[b];
         const Geometry &g = *geoms[b];
@@ -312,6 +334,11 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
                                                                     s.nbr, s.lmask, cell_xr);
             k_plane_offsets<<<blocks_for(P.n_fluid), kBlock, 0, st>>>(s.fluid_cell, begin, end, P.cell_base, nx * ny,
                                                                        nz, s.plane_off + P.poff_base);
+            if (nx < 65536 && ny < 32768) {
+                const int32_t tiles = end / kBlock - begin / kBlock + 1;
+                k_dense_tiles<<<blocks_for(tiles), kBlock, 0, st>>>(s.fluid_cell, s.plane_off + P.poff_base, begin,
+                                                                     end, P.cell_base, nx, ny, nz, s.tile_desc);
+            }
         } else {
             LBM_CUDA_TRY(cudaMemsetAsync(s.plane_off + P.poff_base, 0, sizeof(int32_t) * (nz + 1), st));
         }

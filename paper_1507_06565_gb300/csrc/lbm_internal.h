@@ -107,7 +107,7 @@ struct Part {
 
 // Workspace carve-up.
 struct Layout {
-    size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr;
+    size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr, tile_desc;
     size_t u_cur, u_prev, rho_cur, prof_prev, bins_start, bins_img, scan_tmp, partials, result, total;
     size_t part_shift, part_foff;
     // build-time aliases inside the pdf region
@@ -167,6 +167,11 @@ struct Solver {
     double *link_q = nullptr;
     int32_t *fluid_cell = nullptr;
     int32_t *plane_off = nullptr;
+    // per tile of kBlock cells: {fluid index of cell (0, 0, z) of the tile's
+    // first plane, nx | ny << 16} when every cell of the tile lies in a fully
+    // fluid plane whose neighbour planes are fully fluid too (its neighbour
+    // indices are then arithmetic and it has no wall link), else {-1, 0}
+    int2 *tile_desc = nullptr;
     uint2 *row_words = nullptr;
     uint32_t *cell_xr = nullptr;
     float *u_cur = nullptr;

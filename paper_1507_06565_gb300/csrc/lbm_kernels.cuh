@@ -268,6 +268,22 @@ __device__ __forceinline__ uint32_t row_neighbours(int32_t nb[kQ], const RowGeo 
     return m;
 }
 
+// Neighbour indices of a cell of a dense tile (Solver::tile_desc d): the
+// tile's planes and their neighbours are fully fluid, so the fluid index of
+// (x, y, z) is d.x + x + nx (y + ny (z - z_first)) and a neighbour is a fixed
+// offset, with the periodic wrap in x and y.
+__device__ __forceinline__ void dense_neighbours(int32_t nb[kQ], int2 d, int32_t i)
+{
+    const int nx = d.y & 0xFFFF, ny = d.y >> 16;
+    const int32_t r = i - d.x, plane = nx * ny;
+    const int x = r % nx, y = (r / nx) % ny;
+    const int32_t ox[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? -(nx - 1) : 1};
+    const int32_t oy[3] = {y == 0 ? (ny - 1) * nx : -nx, 0, y == ny - 1 ? -(ny - 1) * nx : nx};
+    nb[0] = i;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) nb[k] = i + ox[ex(k) + 1] + oy[ey(k) + 1] + ez(k) * plane;
+}
+
 __device__ __forceinline__ uint32_t load_nbr(int32_t nb[kQ], const int32_t *__restrict__ nbr, size_t n_pad, int32_t i)
 {
     uint32_t m = 0;

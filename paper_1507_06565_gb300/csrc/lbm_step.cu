@@ -35,6 +35,7 @@ struct StepArgs {
     const int32_t *nbr;
     const uint32_t *lmask;
     const uint32_t *warp_off;
+    const int2 *tile_desc;
     const float *link_a;
     int32_t n_fluid;
     int32_t n_pad;
@@ -94,7 +95,8 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 // collision lowers register pressure and raises the number of resident warps,
 // which is what hides the memory latency of the two dependent loads (indices,
 // then populations).
-// ROWS: neighbour indices from the row bitmasks; otherwise from the table.
+// ROWS: neighbour indices from the row bitmasks; otherwise from the table,
+// except in dense tiles, where they are computed (no index traffic).
 template <typename T, bool ROWS>
 __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock],
                                          float (*a_s)[kBlock])
@@ -104,9 +106,12 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     // 32-bit element offsets (19 n_pad < 2^32 is checked on the host)
     const uint32_t n_pad = (uint32_t)p.n_pad, ui = (uint32_t)i;
     uint32_t m = 0;
+    // a dense tile (same for the whole block) computes its indices and has no links
+    const int2 d = ROWS ? make_int2(-1, 0) : __ldg(p.tile_desc + (i / kBlock));
     if (live) {
         int32_t nb[kQ];
-        m = ROWS ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
+        if (d.x >= 0) dense_neighbours(nb, d, i);
+        else m = ROWS ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
 #pragma unroll
         for (int k = 1; k < kQ; ++k) nb_s[k - 1][t] = nb[k];
     }
@@ -192,6 +197,7 @@ StepArgs<T> make_args(const Solver &s)
     p.nbr = s.nbr;
     p.lmask = s.lmask;
     p.warp_off = s.warp_off;
+    p.tile_desc = s.tile_desc;
     p.link_a = s.link_a;
     p.n_fluid = s.n_fluid;
     p.n_pad = s.n_pad;
