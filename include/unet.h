@@ -5,7 +5,7 @@
  *
  * The paper has no learned component.  The warm start feeds the LBM a better
  * initial velocity u0 (lbm_init evaluates Eq. (equilibrium) at u0); the
- * converged LBM remains the judge of the prediction, so a poor prediction only
+ * converged LBM remains the arbiter of the prediction, so a poor prediction only
  * costs steps, never accuracy.
  *
  * Conventions are those of lbm.h: LBM_* status codes, caller-owned device

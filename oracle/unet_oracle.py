@@ -5,7 +5,7 @@ baseline may use this module; it shares no code with the CUDA library.
 
 The paper has no learned component: the warm start is an addition that feeds
 the LBM of Sec. 2 a better initial velocity (Eq. (equilibrium) evaluated at a
-predicted u0), and the converged LBM stays the judge of its error.  This file
+predicted u0), and the converged LBM stays the arbiter of its error.  This file
 states, plainly and slowly, what the GPU kernels compute:
 
 * ``sdf``: truncated signed distance to the solid (spheres of the packing and

@@ -1,7 +1,7 @@
 // unet.cu -- a 3-D convolutional U-Net that maps the signed-distance field of
 // a geometry to its steady velocity field, used to warm-start the LBM
 // (Eq. (equilibrium) evaluated at the predicted u0).  The paper has no learned
-// component; the converged LBM stays the judge of the prediction's error.
+// component; the converged LBM stays the arbiter of the prediction's error.
 //
 // Architecture (fixed): 4 levels of two 3x3x3 convolutions + ReLU with
 // 16/32/64/128 channels, 2x2x2 average pooling, nearest x2 upsampling with the

@@ -9,7 +9,7 @@
 3. warm start: the network's prediction, scaled back to lattice units,
    initialises lbm_init; the LBM then runs to the same steady-state tolerance
    as a cold start, so the prediction only changes the number of steps, and
-   the converged LBM judges the prediction.
+   the converged LBM is the measure of the prediction.
 
 Every arithmetic step runs in the library's kernels; torch only provides
 device memory (reshapes, copies and slices of tensors).
