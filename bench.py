@@ -39,6 +39,9 @@ WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlappi
 # full-grid launches of all four solvers (see
 # profiles/step_kernels_channel_256x256x512_dram.txt)
 MEASURED_DRAM_B_PER_FLUP = {"even": 155.2, "odd": 181.3}
+# the same for the 64 batched REV cubes (table-only odd step,
+# profiles/step_kernels_rev_64cubes_dram.txt)
+MEASURED_DRAM_B_PER_FLUP_REV = {"even": 158.5, "odd": 226.8}
 # bounded samples of the workload for the CPU oracle: same sphere radius,
 # porosity and channel structure at a reduced box
 SAMPLE = W.Channel("W2-shaped sample 128x128x256 r=8 phi=0.6", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, 0.6, True, 2060)
@@ -681,8 +684,12 @@ def run_ours(args, world, rank, local):
     # dram__bytes_write.sum, profiles/step_kernels_channel_256x256x512_dram.txt):
     # only for the configuration it was taken on
     traffic = None
-    if args.workload == "channel" and args.storage == "f32" and args.odd == "auto":
-        traffic = float(np.mean(nfs)) * 0.5 * (MEASURED_DRAM_B_PER_FLUP["even"] + MEASURED_DRAM_B_PER_FLUP["odd"])
+    if args.storage == "f32" and args.odd == "auto":
+        if args.workload == "channel":
+            traffic = float(np.mean(nfs)) * 0.5 * (MEASURED_DRAM_B_PER_FLUP["even"] + MEASURED_DRAM_B_PER_FLUP["odd"])
+        elif args.workload == "rev" and args.cubes == 64:
+            traffic = float(np.mean(nfs)) * 0.5 * (MEASURED_DRAM_B_PER_FLUP_REV["even"]
+                                                   + MEASURED_DRAM_B_PER_FLUP_REV["odd"])
 
     # end to end through the public API with host buffers: lbm_init from the
     # host geometry (mask and sphere bins copied host->device), E2E_STEPS

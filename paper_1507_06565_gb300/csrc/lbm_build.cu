@@ -382,6 +382,18 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     }
 
     LBM_CUDA_TRY(cudaMemcpyAsync(counts.data(), d_total, sizeof(uint32_t) * counts.size(), cudaMemcpyDeviceToHost, st));
+    {
+        // the span of dense tiles, for the odd step's dense kernel
+        std::vector<int2> desc((size_t)(s.n_pad / kBlock));
+        LBM_CUDA_TRY(cudaMemcpyAsync(desc.data(), s.tile_desc, sizeof(int2) * desc.size(), cudaMemcpyDeviceToHost, st));
+        LBM_CUDA_TRY(cudaStreamSynchronize(st));
+        s.dense_lo = s.dense_hi = 0;
+        for (size_t t = 0; t < desc.size(); ++t)
+            if (desc[t].x >= 0) {
+                if (s.dense_hi == 0) s.dense_lo = (int32_t)t;
+                s.dense_hi = (int32_t)t + 1;
+            }
+    }
     LBM_CUDA_TRY(cudaStreamSynchronize(st));
     for (size_t b = 0; b < s.parts.size(); ++b)
         if ((int64_t)counts[b] != s.parts[b].n_fluid) {

@@ -172,6 +172,7 @@ struct Solver {
     // fluid plane whose neighbour planes are fully fluid too (its neighbour
     // indices are then arithmetic and it has no wall link), else {-1, 0}
     int2 *tile_desc = nullptr;
+    int32_t dense_lo = 0, dense_hi = 0;   // tiles [dense_lo, dense_hi) hold every dense tile
     uint2 *row_words = nullptr;
     uint32_t *cell_xr = nullptr;
     float *u_cur = nullptr;

@@ -26,6 +26,13 @@ namespace {
 // neighbour gathers, which hit L1 about a third of the time.
 constexpr int kEvenBlocksPerSM = 6;
 constexpr int kOddBlocksPerSM = 5;
+
+// Where the odd step takes a cell's neighbour indices from: the table, the
+// row bitmasks, or the table except in dense tiles (Solver::tile_desc), whose
+// indices are computed.  Without dense tiles the table-only kernel is used:
+// it carries no descriptor load or branch (the periodic REV cubes, 2.7% faster
+// in the odd step).
+enum NbSource { kNbTable = 0, kNbRows = 1, kNbDense = 2 };
 constexpr int kGraphSteps = 32;     // steps per CUDA-graph replay (even)
 constexpr int kTuneReps = 3;        // timed launches per candidate grid
 
@@ -36,6 +43,7 @@ struct StepArgs {
     const uint32_t *lmask;
     const uint32_t *warp_off;
     const int2 *tile_desc;
+    int32_t dense_lo, dense_hi;   // every dense tile lies in [dense_lo, dense_hi)
     const float *link_a;
     int32_t n_fluid;
     int32_t n_pad;
@@ -95,9 +103,8 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 // collision lowers register pressure and raises the number of resident warps,
 // which is what hides the memory latency of the two dependent loads (indices,
 // then populations).
-// ROWS: neighbour indices from the row bitmasks; otherwise from the table,
-// except in dense tiles, where they are computed (no index traffic).
-template <typename T, bool ROWS>
+// NB: where the neighbour indices come from (NbSource).
+template <typename T, int NB>
 __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock],
                                          float (*a_s)[kBlock])
 {
@@ -107,11 +114,13 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     const uint32_t n_pad = (uint32_t)p.n_pad, ui = (uint32_t)i;
     uint32_t m = 0;
     // a dense tile (same for the whole block) computes its indices and has no links
-    const int2 d = ROWS ? make_int2(-1, 0) : __ldg(p.tile_desc + (i / kBlock));
+    const int32_t tile = i / kBlock;
+    const int2 d = NB == kNbDense && tile >= p.dense_lo && tile < p.dense_hi ? __ldg(p.tile_desc + tile)
+                                                                            : make_int2(-1, 0);
     if (live) {
         int32_t nb[kQ];
         if (d.x >= 0) dense_neighbours(nb, d, i);
-        else m = ROWS ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
+        else m = NB == kNbRows ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
 #pragma unroll
         for (int k = 1; k < kQ; ++k) nb_s[k - 1][t] = nb[k];
     }
@@ -143,13 +152,13 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
     for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) even_cell(p, tile * kBlock + threadIdx.x);
 }
 
-template <typename T, bool ROWS, int MINB>
+template <typename T, int NB, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
 {
     __shared__ int32_t nb_s[kQ - 1][kBlock];
     __shared__ float a_s[kQ - 1][kBlock];
     for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x)
-        odd_cell<T, ROWS>(p, tile * kBlock + threadIdx.x, nb_s, a_s);
+        odd_cell<T, NB>(p, tile * kBlock + threadIdx.x, nb_s, a_s);
 }
 
 // Initial state f_k = f_k^eq(rho = 1, u0) (Eq. (equilibrium)) stored shifted
@@ -198,6 +207,8 @@ StepArgs<T> make_args(const Solver &s)
     p.lmask = s.lmask;
     p.warp_off = s.warp_off;
     p.tile_desc = s.tile_desc;
+    p.dense_lo = s.dense_lo;
+    p.dense_hi = s.dense_hi;
     p.link_a = s.link_a;
     p.n_fluid = s.n_fluid;
     p.n_pad = s.n_pad;
@@ -231,8 +242,9 @@ void launch_step(const Solver &s, const StepArgs<T> &p, bool odd, int grid, cuda
 {
     const unsigned g = (unsigned)(grid > 0 ? std::min(grid, p.n_tiles) : p.n_tiles);
     if (!odd) k_step_even<T, kEvenBlocksPerSM><<<g, kBlock, 0, st>>>(p);
-    else if (s.odd_rows) k_step_odd<T, true, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
-    else k_step_odd<T, false, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    else if (s.odd_rows) k_step_odd<T, kNbRows, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    else if (p.dense_hi > p.dense_lo) k_step_odd<T, kNbDense, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    else k_step_odd<T, kNbTable, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
 }
 
 // Candidate grids: a block per tile, or 1, 2, 4 waves of resident blocks
