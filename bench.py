@@ -211,6 +211,8 @@ def odd_flags(args) -> int:
              "rows": L.LBM_FLAG_ROW_NEIGHBOURS}[getattr(args, "odd", "auto")]
     if getattr(args, "bounce_back", False):
         flags |= L.LBM_FLAG_SIMPLE_BOUNCE_BACK
+    if getattr(args, "even", "auto") == "staged":
+        flags |= L.LBM_FLAG_STAGED_EVEN
     return flags
 
 
@@ -718,7 +720,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage, "odd_neighbours": args.odd,
+        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage, "odd_neighbours": args.odd, "even_step": args.even,
                    "schedule": schedules,
                    "l2": "inputs larger than L2 ({:.1f}-{:.1f} GB of populations and indices per solver)".format(
                        *(n * (19 * (4 if args.storage == "f32" else 2) + 76) / 1e9 for n in (min(nfs), max(nfs)))),
@@ -751,6 +753,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--odd", choices=["auto", "table", "rows"], default="auto",
                     help="neighbour indices of the odd step (library default, int32 table, row bitmasks)")
+    ap.add_argument("--even", choices=["auto", "staged"], default="auto",
+                    help="even-step kernel: autotuned, or always the TMA-staged one")
     ap.add_argument("--bounce-back", action="store_true",
                     help="simple bounce-back on every wall link instead of CLI (Eq. (noslip), q = 1/2 forced)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",

@@ -109,6 +109,10 @@ typedef struct {
  * steps in chunks as a CUDA graph.  These flags turn either off. */
 #define LBM_FLAG_NO_GRAPH 4
 #define LBM_FLAG_NO_AUTOTUNE 8
+/* The even step always on its staged kernel (populations fetched into shared
+ * memory by TMA bulk copies), which the autotuner otherwise tries as one of its
+ * candidates.  Same arithmetic, same results. */
+#define LBM_FLAG_STAGED_EVEN 64
 /* Simple bounce-back (Eq. (noslip): every wall surface half-way along its
  * link, q = 1/2 forced) on every wall link instead of Eq. (CLI).  The link
  * fractions q are still computed and exported; every link reports the
@@ -211,8 +215,10 @@ int lbm_batch_profile_residual(lbm_solver *solver, double *res_out);
 
 /* Launch schedule in use: grid sizes of the even and odd step kernels (the
  * kernels loop over tiles of 256 fluid cells, so a grid smaller than the tile
- * count makes them persistent), whether the autotuner has finished, and the
- * steps per CUDA-graph replay (0: graphs off). */
+ * count makes them persistent; grid_even = -1: the even step's staged kernel,
+ * which fetches each tile's populations into shared memory with TMA bulk
+ * copies, on one wave of resident blocks), whether the autotuner has
+ * finished, and the steps per CUDA-graph replay (0: graphs off). */
 int lbm_schedule(const lbm_solver *solver, int32_t *grid_even, int32_t *grid_odd, int32_t *tuned,
                  int32_t *graph_steps);
 

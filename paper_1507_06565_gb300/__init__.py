@@ -35,6 +35,7 @@ LBM_FLAG_ROW_NEIGHBOURS = 2
 LBM_FLAG_NO_GRAPH = 4
 LBM_FLAG_NO_AUTOTUNE = 8
 LBM_FLAG_SIMPLE_BOUNCE_BACK = 32
+LBM_FLAG_STAGED_EVEN = 64
 
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1

@@ -66,6 +66,7 @@ Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size
     L.result = take((res_part(L, L.n_parts) + 8) * 8);
     L.part_shift = take((size_t)L.n_parts * 4);
     L.part_foff = take((size_t)(L.n_parts + 1) * 4);
+    L.status = take(sizeof(int));
     L.total = off;
     return L;
 }
@@ -104,7 +105,7 @@ static bool params_ok(const lbm_params *p)
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return false;
     const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE |
-                          LBM_FLAG_SIMPLE_BOUNCE_BACK;
+                          LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_STAGED_EVEN;
     if ((p->flags & ~known) != 0) return false;
     if ((p->flags & LBM_FLAG_NEIGHBOUR_TABLE) && (p->flags & LBM_FLAG_ROW_NEIGHBOURS)) return false;
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
@@ -215,6 +216,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->result = (double *)(s->ws + L.result);
     s->part_shift = (float *)(s->ws + L.part_shift);
     s->part_foff = (int32_t *)(s->ws + L.part_foff);
+    s->status = (int *)(s->ws + L.status);
     const bool single = geoms.size() == 1;
     s->n_words = (s->box.nx + 31) / 32;
     s->x_bits = x_bits_for(s->box.nx);
@@ -226,6 +228,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     }
     s->use_graph = !(params->flags & LBM_FLAG_NO_GRAPH);
     s->autotune = !(params->flags & LBM_FLAG_NO_AUTOTUNE);
+    s->staged_even = (params->flags & LBM_FLAG_STAGED_EVEN) != 0;
     std::vector<int32_t> foff;
     for (const Part &P : s->parts) foff.push_back(P.fluid_off);
     foff.push_back(s->n_fluid);
@@ -375,6 +378,22 @@ int lbm_batch_part_info(const lbm_solver *s, int32_t part, lbm_geometry_info *in
     return LBM_OK;
 }
 
+// Synchronise the solver's stream and read the step kernels' status word:
+// LBM_ETIMEOUT (and the word cleared) if a bounded device-side wait gave up
+// since the last check.
+static int sync_checked(lbm_solver *s)
+{
+    int st = 0;
+    if (cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    if (st) {
+        if (cudaMemsetAsync(s->status, 0, sizeof(int), s->stream) != cudaSuccess) return LBM_ECUDA;
+        return LBM_ETIMEOUT;
+    }
+    return LBM_OK;
+}
+
 int lbm_batch_permeability(lbm_solver *s, double *k_out)
 {
     if (!s || !k_out || s->params.g[0] == 0.0) return LBM_EINVAL;
@@ -386,7 +405,7 @@ int lbm_batch_permeability(lbm_solver *s, double *k_out)
     if (cudaMemcpyAsync(r.data(), s->result + res_part(s->lay, 0), r.size() * sizeof(double), cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess)
         return LBM_ECUDA;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+    if (int rc = sync_checked(s)) return rc;
     for (size_t b = 0; b < s->parts.size(); ++b) k_out[b] = r[8 * b];
     return LBM_OK;
 }
@@ -419,7 +438,7 @@ int lbm_plane_average(lbm_solver *s, double *host_out)
     if (cudaMemcpyAsync(host_out, s->result, sizeof(double) * 3 * (size_t)s->lay.n_planes, cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess)
         return LBM_ECUDA;
-    return cudaStreamSynchronize(s->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    return sync_checked(s);
 }
 
 int lbm_permeability(lbm_solver *s, int32_t z_lo, int32_t z_hi, double *k_out)
@@ -435,7 +454,7 @@ int lbm_permeability(lbm_solver *s, int32_t z_lo, int32_t z_hi, double *k_out)
     if (cudaMemcpyAsync(k_out, s->result + res_part(s->lay, 0), sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
         cudaSuccess)
         return LBM_ECUDA;
-    return cudaStreamSynchronize(s->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    return sync_checked(s);
 }
 
 int lbm_residual(lbm_solver *s, double *res_out)
@@ -447,7 +466,7 @@ int lbm_residual(lbm_solver *s, double *res_out)
     if (cudaMemcpyAsync(r, s->result + res_field(s->lay), sizeof(r), cudaMemcpyDeviceToHost, s->stream) !=
         cudaSuccess)
         return LBM_ECUDA;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+    if (int rc2 = sync_checked(s)) return rc2;
     const bool had_prev = s->has_prev;
     std::swap(s->u_cur, s->u_prev);
     s->has_prev = true;
@@ -468,7 +487,7 @@ static int profile_residuals(lbm_solver *s, double *per_part, double *worst)
     if (cudaMemcpyAsync(r.data(), s->result + res_part(s->lay, 0), r.size() * sizeof(double), cudaMemcpyDeviceToHost,
                         s->stream) != cudaSuccess)
         return LBM_ECUDA;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+    if (int rc2 = sync_checked(s)) return rc2;
     double w = 0.0;
     bool bad = false;
     for (size_t b = 0; b < s->parts.size(); ++b) {
@@ -516,7 +535,7 @@ static int part_masses(lbm_solver *s, std::vector<double> &per_part, double *mea
                         s->stream) != cudaSuccess ||
         cudaMemcpyAsync(g, s->result + res_mass(s->lay), sizeof(g), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
         return LBM_ECUDA;
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBM_ECUDA;
+    if (int rc2 = sync_checked(s)) return rc2;
     bool bad = g[1] != 0.0 || !std::isfinite(g[0]);
     for (size_t b = 0; b < s->parts.size(); ++b) {
         bad |= r[8 * b + 5] != 0.0 || !std::isfinite(r[8 * b + 4]);

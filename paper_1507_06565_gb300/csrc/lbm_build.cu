@@ -315,6 +315,7 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     std::vector<uint32_t> counts(s.parts.size() + 1, 0);
 
     LBM_CUDA_TRY(cudaMemsetAsync(s.tile_desc, 0xFF, sizeof(int2) * (s.n_pad / kBlock), st));
+    LBM_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int), st));
     for (size_t b = 0; b < s.parts.size(); ++b) {
         const Part &P = s.parts[b];
         const Geometry &g = *geoms[b];

@@ -109,7 +109,7 @@ struct Part {
 struct Layout {
     size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr, tile_desc;
     size_t u_cur, u_prev, rho_cur, prof_prev, bins_start, bins_img, scan_tmp, partials, result, total;
-    size_t part_shift, part_foff;
+    size_t part_shift, part_foff, status;
     // build-time aliases inside the pdf region
     size_t idx_map, mask;
     int32_t n_pad;
@@ -144,11 +144,12 @@ struct Solver {
     int n_words = 0;               // 32-cell words per row (single part)
     int x_bits = 0;                // bits of x in cell_xr
     bool odd_rows = true;          // odd step computes neighbours from row bitmasks
-    // launch schedule: grid sizes of the even/odd step (0 = one block per tile)
+    // launch schedule: grid sizes of the even/odd step (0 = one block per
+    // tile, -1 = the staged even kernel on one wave of resident blocks)
     int grid_even = 0, grid_odd = 0;
     int tune_state = 0;            // 0 untuned, 1 tuning, 2 done
     int tune_idx = 0;
-    std::vector<int> tune_grids;
+    std::vector<int> tune_grids_even, tune_grids_odd;   // candidates (-1: staged even kernel)
     std::vector<float> tune_ms_even, tune_ms_odd;
     int tune_count_even = 0, tune_count_odd = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -158,6 +159,7 @@ struct Solver {
     cudaGraphExec_t graph_exec = nullptr;
     bool use_graph = true;
     bool autotune = true;
+    bool staged_even = false;      // LBM_FLAG_STAGED_EVEN
     // device pointers
     void *pdf = nullptr;
     int32_t *nbr = nullptr;
@@ -183,6 +185,7 @@ struct Solver {
     double *result = nullptr;
     float *part_shift = nullptr;
     int32_t *part_foff = nullptr;
+    int *status = nullptr;   // set by a step kernel whose bounded wait gave up
     ~Solver();
 };
 

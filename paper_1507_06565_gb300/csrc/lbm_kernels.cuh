@@ -45,6 +45,57 @@ __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
+// ---- TMA bulk copies global -> shared memory, completed on an mbarrier ----
+// A copy moves a contiguous run of bytes (16-byte aligned at both ends, a
+// multiple of 16 bytes long); the barrier's phase completes once the bytes
+// announced with expect_tx have landed.  Waits are bounded: a wait that gives
+// up returns false and the caller reports LBM_ETIMEOUT instead of hanging.
+namespace bulk {
+constexpr int kMaxPolls = 1 << 22;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+// makes barrier initialisation visible to the async proxy (the TMA unit)
+__device__ __forceinline__ void fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(saddr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < kMaxPolls; ++it)
+        if (test(bar, parity)) return true;
+    return false;
+}
+}  // namespace bulk
+
 // Relaxation constants and source term of one solver (kernel parameter).
 struct Coef {
     float omega_p, omega_m;
@@ -156,27 +207,48 @@ __device__ __forceinline__ void moments(const float h[kQ], float &drho, float &j
     }
 }
 
+// e_k . j from the non-zero components only (exact: e_k has entries 0, +-1).
+__device__ __forceinline__ float e_dot(int k, float jx, float jy, float jz)
+{
+    float s = 0.0f;
+    bool any = false;
+    if (ex(k)) {
+        s = ex(k) > 0 ? jx : -jx;
+        any = true;
+    }
+    if (ey(k)) {
+        s = any ? __fadd_rn(s, ey(k) > 0 ? jy : -jy) : (ey(k) > 0 ? jy : -jy);
+        any = true;
+    }
+    if (ez(k)) s = any ? __fadd_rn(s, ez(k) > 0 ? jz : -jz) : (ez(k) > 0 ? jz : -jz);
+    return s;
+}
+
 // TRT collision with source (Eqs. (TRT), (TRT2), (equilibrium), (collision)),
 // on shifted populations: h~_k = h_k - w+ (h_k^+ - e_k^+) - w- (h_k^- - e_k^-) + F_k,
 // e_k^+ = w_k (drho + 9/2 (e.j)^2 - 3/2 j.j), e_k^- = 3 w_k e.j, with the
-// pre-collision momentum j.
+// pre-collision momentum j.  Every rounding is spelled out (fmaf, __fmul_rn,
+// __fadd_rn: the compiler may not contract or reorder them), so all step
+// kernels produce the same bits for the same inputs whatever code surrounds
+// the collision.
 __device__ __forceinline__ void collide(float h[kQ], const Coef &c)
 {
     float drho, jx, jy, jz;
     moments(h, drho, jx, jy, jz);
-    const float usq = 1.5f * (jx * jx + jy * jy + jz * jz);
-    h[0] -= c.omega_p * (h[0] - (float)weight(0) * (drho - usq));
+    const float usq = __fmul_rn(1.5f, fmaf(jz, jz, fmaf(jy, jy, __fmul_rn(jx, jx))));
+    const float e0 = __fmul_rn((float)weight(0), __fsub_rn(drho, usq));
+    h[0] = fmaf(-c.omega_p, __fsub_rn(h[0], e0), h[0]);
 #pragma unroll
     for (int k = 1; k < kQ; k += 2) {
         const int kb = k + 1;
-        const float eu = (float)ex(k) * jx + (float)ey(k) * jy + (float)ez(k) * jz;
+        const float eu = e_dot(k, jx, jy, jz);
         const float w = (float)weight(k);
-        const float ep = w * (drho + 4.5f * eu * eu - usq);
-        const float em = 3.0f * w * eu;
-        const float dp = c.omega_p * (0.5f * (h[k] + h[kb]) - ep);
-        const float dm = c.omega_m * (0.5f * (h[k] - h[kb]) - em);
-        const float hk = h[k] - dp - dm + c.force[k];
-        const float hb = h[kb] - dp + dm - c.force[k];
+        const float ep = __fmul_rn(w, __fsub_rn(fmaf(__fmul_rn(4.5f, eu), eu, drho), usq));
+        const float em = __fmul_rn(3.0f * w, eu);
+        const float dp = __fmul_rn(c.omega_p, fmaf(0.5f, __fadd_rn(h[k], h[kb]), -ep));
+        const float dm = __fmul_rn(c.omega_m, fmaf(0.5f, __fsub_rn(h[k], h[kb]), -em));
+        const float hk = __fadd_rn(__fsub_rn(__fsub_rn(h[k], dp), dm), c.force[k]);
+        const float hb = __fsub_rn(__fadd_rn(__fsub_rn(h[kb], dp), dm), c.force[k]);
         h[k] = hk;
         h[kb] = hb;
     }

@@ -33,6 +33,7 @@ constexpr int kOddBlocksPerSM = 5;
 // it carries no descriptor load or branch (the periodic REV cubes, 2.7% faster
 // in the odd step).
 enum NbSource { kNbTable = 0, kNbRows = 1, kNbDense = 2 };
+constexpr int kGridBulk = -1;       // schedule entry: the staged even step
 constexpr int kGraphSteps = 32;     // steps per CUDA-graph replay (even)
 constexpr int kTuneReps = 3;        // timed launches per candidate grid
 
@@ -45,6 +46,7 @@ struct StepArgs {
     const int2 *tile_desc;
     int32_t dense_lo, dense_hi;   // every dense tile lies in [dense_lo, dense_hi)
     const float *link_a;
+    int *status;   // set to 1 when a bounded wait gives up
     int32_t n_fluid;
     int32_t n_pad;
     int32_t n_tiles;
@@ -152,6 +154,84 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
     for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) even_cell(p, tile * kBlock + threadIdx.x);
 }
 
+// Even step with the populations staged through shared memory.  A persistent
+// block takes the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0
+// fetches each tile's 19 rows (kBlock contiguous slots per direction, 16-byte
+// aligned since n_pad and the tiles are multiples of 256 cells) with TMA bulk
+// copies into one of S stages, S tiles ahead of the collision.  The bytes in
+// flight are then set by the stages, not by the registers of the resident
+// threads, which is what limits the register-staged kernel in 16-bit storage
+// (38 B in flight per thread).  Results are stored directly (stores need no
+// latency hiding).  A stage is refilled after the block barrier that follows
+// its last read.
+template <typename T, int S>
+constexpr size_t even_bulk_smem()
+{
+    return (size_t)S * kQ * kBlock * sizeof(T) + (size_t)S * sizeof(uint64_t);
+}
+
+template <typename T, int S, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *buf = (T *)smem_raw;   // [S][kQ][kBlock]
+    uint64_t *full = (uint64_t *)(smem_raw + (size_t)S * kQ * kBlock * sizeof(T));
+    constexpr uint32_t kRow = kBlock * sizeof(T);
+    const int t = threadIdx.x;
+    const int32_t first = blockIdx.x, stride = gridDim.x;
+    const int32_t count = first < p.n_tiles ? (p.n_tiles - 1 - first) / stride + 1 : 0;
+    const size_t n_pad = (size_t)p.n_pad;
+    auto issue = [&](int32_t j) {   // warp 0
+        const int st_ = j % S;
+        const size_t base = (size_t)(first + j * stride) * kBlock;
+        const int lane = t & 31;
+        if (lane == 0) bulk::expect_tx(&full[st_], kQ * kRow);
+        __syncwarp();
+        if (lane < kQ) bulk::copy(buf + ((size_t)st_ * kQ + lane) * kBlock, p.pdf + lane * n_pad + base, kRow, &full[st_]);
+    };
+    if (t == 0) {
+        for (int q = 0; q < S; ++q) bulk::init(&full[q], 1);
+        bulk::fence_init();
+    }
+    __syncthreads();
+    if (t < 32)
+        for (int32_t j = 0; j < S && j < count; ++j) issue(j);
+    int32_t j = 0;
+    bool ok = true;
+    for (; j < count; ++j) {
+        const int32_t i = (first + j * stride) * kBlock + t;
+        const bool live = i < p.n_fluid;
+        const uint32_t m = live ? p.lmask[i] : 0u;
+        const uint32_t off = first_link(p.warp_off, i, m);
+        const T *row = buf + (size_t)(j % S) * kQ * kBlock + t;
+        ok = bulk::wait(&full[j % S], (uint32_t)((j / S) & 1));
+        float h[kQ];
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) h[k] = ok ? ld(row + k * kBlock) : 0.0f;
+        if (__syncthreads_or(!ok)) break;   // the stage is free again
+        if (t < 32 && j + S < count) issue(j + S);
+        if (!live) continue;
+        if (m) {
+#pragma unroll
+            for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(link_coef(p.link_a, off, m, k), h[k], h[opp(k)]);
+        }
+        if (p.shift_on) apply_shift(h, part_shift_of(p, i));
+        collide(h, p.c);
+        if (m) {
+#pragma unroll
+            for (int k = 1; k < kQ; ++k) h[k] = fmaf(-link_coef(p.link_a, off, m, k), h[opp(k)], h[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) st(p.pdf + opp(k) * n_pad + i, h[k]);
+    }
+    if (j < count && t == 0) {
+        // a wait gave up: report it, and let the copies still in flight land
+        // before the block's shared memory is released
+        atomicExch(p.status, 1);
+        for (int32_t q = j; q < count && q < j + S; ++q) bulk::wait(&full[q % S], (uint32_t)((q / S) & 1));
+    }
+}
+
 template <typename T, int NB, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
 {
@@ -210,6 +290,7 @@ StepArgs<T> make_args(const Solver &s)
     p.dense_lo = s.dense_lo;
     p.dense_hi = s.dense_hi;
     p.link_a = s.link_a;
+    p.status = s.status;
     p.n_fluid = s.n_fluid;
     p.n_pad = s.n_pad;
     p.n_tiles = s.n_pad / kBlock;
@@ -236,30 +317,67 @@ int sm_count()
     return n > 0 ? n : 1;
 }
 
-// One step launch at the current parity with the chosen grid (0: a block per tile).
+// Stages and resident blocks of the staged even step per storage type.
+template <typename T>
+struct EvenBulk {
+    static constexpr int S = 2, MINB = 5;   // FP32: 39 KB of stages per block
+};
+template <>
+struct EvenBulk<__half> {
+    static constexpr int S = 4, MINB = 5;
+};
+template <>
+struct EvenBulk<__nv_bfloat16> {
+    static constexpr int S = 4, MINB = 5;
+};
+
+// The staged even step on one wave of resident blocks.
+template <typename T, int S, int MINB>
+void launch_even_bulk(const StepArgs<T> &p, cudaStream_t st)
+{
+    constexpr size_t smem = even_bulk_smem<T, S>();
+    static const int wave = [] {
+        cudaFuncSetAttribute(k_step_even_bulk<T, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_even_bulk<T, S, MINB>, kBlock, smem) !=
+            cudaSuccess)
+            nb = 1;
+        return sm_count() * std::max(nb, 1);
+    }();
+    k_step_even_bulk<T, S, MINB><<<(unsigned)std::min(wave, p.n_tiles), kBlock, smem, st>>>(p);
+}
+
+// One step launch at the current parity with the chosen grid (0: a block per
+// tile; kGridBulk: the staged even step).
 template <typename T>
 void launch_step(const Solver &s, const StepArgs<T> &p, bool odd, int grid, cudaStream_t st)
 {
     const unsigned g = (unsigned)(grid > 0 ? std::min(grid, p.n_tiles) : p.n_tiles);
-    if (!odd) k_step_even<T, kEvenBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    if (!odd && grid == kGridBulk) launch_even_bulk<T, EvenBulk<T>::S, EvenBulk<T>::MINB>(p, st);
+    else if (!odd) k_step_even<T, kEvenBlocksPerSM><<<g, kBlock, 0, st>>>(p);
     else if (s.odd_rows) k_step_odd<T, kNbRows, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
     else if (p.dense_hi > p.dense_lo) k_step_odd<T, kNbDense, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
     else k_step_odd<T, kNbTable, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
 }
 
-// Candidate grids: a block per tile, or 1, 2, 4 waves of resident blocks
-// looping over the tiles.  Only solvers of more than four waves are tuned.
+// Candidate schedules: a block per tile, or 1, 2, 4 waves of resident blocks
+// looping over the tiles; the even step also tries its staged kernel.  Only
+// solvers of more than four waves are tuned.
 void start_tuning(Solver &s, int n_tiles)
 {
     const int wave = sm_count() * kOddBlocksPerSM;
-    s.tune_grids = {0};
+    s.tune_grids_odd = {0};
     if (s.autotune && n_tiles > 4 * sm_count() * kEvenBlocksPerSM)
-        for (int w : {1, 2, 4}) s.tune_grids.push_back(w * wave);
-    s.tune_ms_even.assign(s.tune_grids.size(), 0.0f);
-    s.tune_ms_odd.assign(s.tune_grids.size(), 0.0f);
+        for (int w : {1, 2, 4}) s.tune_grids_odd.push_back(w * wave);
+    s.tune_grids_even = s.tune_grids_odd;
+    if (s.staged_even) s.tune_grids_even = {kGridBulk};
+    else if (s.tune_grids_even.size() > 1) s.tune_grids_even.push_back(kGridBulk);
+    s.tune_ms_even.assign(s.tune_grids_even.size(), 0.0f);
+    s.tune_ms_odd.assign(s.tune_grids_odd.size(), 0.0f);
     s.tune_count_even = s.tune_count_odd = 0;
-    s.tune_state = s.tune_grids.size() > 1 ? 1 : 2;
-    s.grid_even = s.grid_odd = 0;
+    s.tune_state = s.tune_grids_odd.size() > 1 ? 1 : 2;
+    s.grid_even = s.staged_even ? kGridBulk : 0;
+    s.grid_odd = 0;
     if (s.tune_state == 1 && (!s.ev0 || !s.ev1)) {
         if (cudaEventCreate(&s.ev0) != cudaSuccess || cudaEventCreate(&s.ev1) != cudaSuccess) s.tune_state = 2;
     }
@@ -274,7 +392,7 @@ int run_steps(Solver &s, int64_t n)
     }
     StepArgs<T> p = make_args<T>(s);
     if (s.tune_state == 0) start_tuning(s, p.n_tiles);
-    const int C = (int)s.tune_grids.size();
+    const int Ce = (int)s.tune_grids_even.size(), Co = (int)s.tune_grids_odd.size();
     int64_t t = 0;
     while (t < n) {
         const bool odd = (s.steps & 1) != 0;
@@ -282,10 +400,11 @@ int run_steps(Solver &s, int64_t n)
         s.shift_pending = false;
         if (s.tune_state == 1) {
             int &cnt = odd ? s.tune_count_odd : s.tune_count_even;
-            if (cnt < C * kTuneReps) {
+            const std::vector<int> &grids = odd ? s.tune_grids_odd : s.tune_grids_even;
+            if (cnt < (int)grids.size() * kTuneReps) {
                 const int c = cnt / kTuneReps;
                 if (cudaEventRecord(s.ev0, s.stream) != cudaSuccess) return LBM_ECUDA;
-                launch_step(s, p, odd, s.tune_grids[c], s.stream);
+                launch_step(s, p, odd, grids[c], s.stream);
                 if (cudaEventRecord(s.ev1, s.stream) != cudaSuccess || cudaEventSynchronize(s.ev1) != cudaSuccess)
                     return LBM_ECUDA;
                 float ms = 0.0f;
@@ -295,11 +414,11 @@ int run_steps(Solver &s, int64_t n)
             } else {
                 launch_step(s, p, odd, odd ? s.grid_odd : s.grid_even, s.stream);
             }
-            if (s.tune_count_even >= C * kTuneReps && s.tune_count_odd >= C * kTuneReps) {
-                s.grid_even = s.tune_grids[std::min_element(s.tune_ms_even.begin(), s.tune_ms_even.end()) -
-                                           s.tune_ms_even.begin()];
-                s.grid_odd = s.tune_grids[std::min_element(s.tune_ms_odd.begin(), s.tune_ms_odd.end()) -
-                                          s.tune_ms_odd.begin()];
+            if (s.tune_count_even >= Ce * kTuneReps && s.tune_count_odd >= Co * kTuneReps) {
+                s.grid_even = s.tune_grids_even[std::min_element(s.tune_ms_even.begin(), s.tune_ms_even.end()) -
+                                                s.tune_ms_even.begin()];
+                s.grid_odd = s.tune_grids_odd[std::min_element(s.tune_ms_odd.begin(), s.tune_ms_odd.end()) -
+                                              s.tune_ms_odd.begin()];
                 s.tune_state = 2;
             }
             ++s.steps;
@@ -383,7 +502,7 @@ extern "C" int lbm_schedule(const lbm_solver *s, int32_t *grid_even, int32_t *gr
 {
     if (!s) return LBM_EINVAL;
     const int32_t tiles = s->n_pad / lbm::kBlock;
-    if (grid_even) *grid_even = s->grid_even > 0 ? std::min(s->grid_even, tiles) : tiles;
+    if (grid_even) *grid_even = s->grid_even > 0 ? std::min(s->grid_even, tiles) : (s->grid_even < 0 ? -1 : tiles);
     if (grid_odd) *grid_odd = s->grid_odd > 0 ? std::min(s->grid_odd, tiles) : tiles;
     if (tuned) *tuned = s->tune_state == 2 ? 1 : 0;
     if (graph_steps_out) *graph_steps_out = s->use_graph ? lbm::graph_steps() : 0;

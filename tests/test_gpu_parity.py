@@ -31,12 +31,12 @@ def torch_cuda():
     return torch
 
 
-def _pair(torch, case, storage="f32", u0=None, g=None):
+def _pair(torch, case, storage="f32", u0=None, g=None, flags=0):
     g = case.g if g is None else g
     geom = L.lbm_geometry_from_spheres(*case.sphere_args(), q_lo=case.q_lo, q_hi=case.q_hi)
     sp = geom.spheres()
     u0_t = None if u0 is None else torch.from_numpy(u0).cuda()
-    solver = L.Solver(geom, case.tau, case.lam, g, storage, u0=u0_t)
+    solver = L.Solver(geom, case.tau, case.lam, g, storage, u0=u0_t, flags=flags)
     lat = O.Lattice(case.nx, case.ny, case.nz, case.periodic_z, sp, case.tau, case.lam, g, case.q_lo,
                     case.q_hi).init(None if u0 is None else u0.astype(np.float64))
     return solver, lat, geom
@@ -64,11 +64,13 @@ def test_lists_bit_exact(torch_cuda, case):
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
 @pytest.mark.parametrize("nsteps", [0, 1, 2, 3, 10])
-def test_populations_step_by_step(torch_cuda, case, nsteps):
+@pytest.mark.parametrize("flags", [0, L.LBM_FLAG_STAGED_EVEN], ids=["plain", "staged-even"])
+def test_populations_step_by_step(torch_cuda, case, nsteps, flags):
     """Both AA parities: the shifted populations after n steps from a warm
-    start, at every fluid cell and direction."""
+    start, at every fluid cell and direction; with the even step on either
+    kernel (registers, or TMA-staged through shared memory)."""
     u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=100 + nsteps, amplitude=2e-2)
-    solver, lat, _ = _pair(torch_cuda, case, u0=u0, g=(3e-5, -1e-5, 2e-5))
+    solver, lat, _ = _pair(torch_cuda, case, u0=u0, g=(3e-5, -1e-5, 2e-5), flags=flags)
     solver.step(nsteps)
     lat.step(nsteps)
     fluid = solver.export_lists()["fluid_cell"]
@@ -260,7 +262,7 @@ def test_step_zero_and_reset(torch_cuda):
 
 
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 1.6e-2)])
-@pytest.mark.parametrize("flags", [0, 1, 2])
+@pytest.mark.parametrize("flags", [0, 1, 2, 64])
 def test_reduced_precision_storage(torch_cuda, storage, tol, flags):
     """FP16/BF16 storage of the shifted populations (FP32 collision): the
     velocity after a few steps stays within the storage's relative precision
@@ -279,6 +281,29 @@ def test_reduced_precision_storage(torch_cuda, storage, tol, flags):
     _, u = solver.moments()
     _, u_o = lat.moments()
     assert np.max(np.abs(u.cpu().numpy() - u_o)) <= tol * np.max(np.abs(u_o))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c.name)
+def test_staged_even_step_bit_exact(torch_cuda, storage, case):
+    """The TMA-staged even kernel performs the register kernel's arithmetic
+    (every rounding of the collision is explicit) on the same values: the
+    states agree bit for bit after both parities, at every storage type (a
+    tile count that is not a multiple of the grid leaves the last blocks with
+    fewer tiles)."""
+    import torch
+
+    u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=11, amplitude=2e-2)
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args(), q_lo=case.q_lo, q_hi=case.q_hi)
+    u0t = torch.from_numpy(u0).cuda()
+    a = L.Solver(geom, case.tau, case.lam, (3e-5, -1e-5, 2e-5), storage, u0=u0t, flags=L.LBM_FLAG_STAGED_EVEN)
+    b = L.Solver(geom, case.tau, case.lam, (3e-5, -1e-5, 2e-5), storage, u0=u0t, flags=L.LBM_FLAG_NO_AUTOTUNE)
+    for n in (1, 1, 9, 40):
+        a.step(n)
+        b.step(n)
+        assert torch.equal(a.populations(), b.populations()), n
+    assert a.schedule()["grid_even"] == -1 and b.schedule()["grid_even"] > 0
+    a.residual()   # synchronises and reads the kernels' timeout word (LBMError if set)
 
 
 @pytest.mark.parametrize("flags", [1, 2])
