@@ -45,6 +45,25 @@ __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
 __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
+// The step kernels work in storage units: FP16 values stay scaled by 2^14
+// through the collision (its constants carry the scale, see Coef), which
+// saves the two multiplications per population and changes no bit, since
+// every scaling is by a power of two.
+template <typename T>
+struct StoreScale {
+    static constexpr float v = 1.0f;
+};
+template <>
+struct StoreScale<__half> {
+    static constexpr float v = kHalfScale;
+};
+__device__ __forceinline__ float ld_raw(const float *p) { return *p; }
+__device__ __forceinline__ float ld_raw(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float ld_raw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st_raw(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_raw(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st_raw(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
 // ---- TMA bulk copies global -> shared memory, completed on an mbarrier ----
 // A copy moves a contiguous run of bytes (16-byte aligned at both ends, a
 // multiple of 16 bytes long); the barrier's phase completes once the bytes
@@ -99,7 +118,8 @@ __device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity)
 // Relaxation constants and source term of one solver (kernel parameter).
 struct Coef {
     float omega_p, omega_m;
-    float force[kQ];   // F_k = 3 w_k e_k.g
+    float usq_c, eu_c;   // 3/2 and 9/2 over the storage scale (quadratic terms)
+    float force[kQ];     // F_k = 3 w_k e_k.g, times the storage scale
     float half_g[3];   // g/2, added to j for the reported velocity
 };
 
@@ -118,8 +138,11 @@ Coef make_coef(const Solver &s);
 // First link index of cell i and its link mask.  Must be called by all 32
 // lanes of a warp with lanes mapped to the aligned cells 32w .. 32w+31; m is
 // this lane's mask (0 for padding lanes).
+template <bool SKIP = true>
 __device__ __forceinline__ uint32_t first_link(const uint32_t *__restrict__ warp_off, int32_t i, uint32_t m)
 {
+    // SKIP: no link in the warp, no scan (the offset is then never used)
+    if (SKIP && !__any_sync(0xffffffffu, m != 0u)) return 0u;
     const uint32_t cnt = __popc(m);
     uint32_t incl = cnt;
     const int lane = threadIdx.x & 31;
@@ -227,7 +250,8 @@ __device__ __forceinline__ float e_dot(int k, float jx, float jy, float jz)
 // TRT collision with source (Eqs. (TRT), (TRT2), (equilibrium), (collision)),
 // on shifted populations: h~_k = h_k - w+ (h_k^+ - e_k^+) - w- (h_k^- - e_k^-) + F_k,
 // e_k^+ = w_k (drho + 9/2 (e.j)^2 - 3/2 j.j), e_k^- = 3 w_k e.j, with the
-// pre-collision momentum j.  Every rounding is spelled out (fmaf, __fmul_rn,
+// pre-collision momentum j.  h is in storage units (Coef carries the scale of
+// the quadratic terms and of F_k).  Every rounding is spelled out (fmaf, __fmul_rn,
 // __fadd_rn: the compiler may not contract or reorder them), so all step
 // kernels produce the same bits for the same inputs whatever code surrounds
 // the collision.
@@ -235,7 +259,7 @@ __device__ __forceinline__ void collide(float h[kQ], const Coef &c)
 {
     float drho, jx, jy, jz;
     moments(h, drho, jx, jy, jz);
-    const float usq = __fmul_rn(1.5f, fmaf(jz, jz, fmaf(jy, jy, __fmul_rn(jx, jx))));
+    const float usq = __fmul_rn(c.usq_c, fmaf(jz, jz, fmaf(jy, jy, __fmul_rn(jx, jx))));
     const float e0 = __fmul_rn((float)weight(0), __fsub_rn(drho, usq));
     h[0] = fmaf(-c.omega_p, __fsub_rn(h[0], e0), h[0]);
 #pragma unroll
@@ -243,7 +267,7 @@ __device__ __forceinline__ void collide(float h[kQ], const Coef &c)
         const int kb = k + 1;
         const float eu = e_dot(k, jx, jy, jz);
         const float w = (float)weight(k);
-        const float ep = __fmul_rn(w, __fsub_rn(fmaf(__fmul_rn(4.5f, eu), eu, drho), usq));
+        const float ep = __fmul_rn(w, __fsub_rn(fmaf(__fmul_rn(c.eu_c, eu), eu, drho), usq));
         const float em = __fmul_rn(3.0f * w, eu);
         const float dp = __fmul_rn(c.omega_p, fmaf(0.5f, __fadd_rn(h[k], h[kb]), -ep));
         const float dm = __fmul_rn(c.omega_m, fmaf(0.5f, __fsub_rn(h[k], h[kb]), -em));
