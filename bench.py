@@ -38,7 +38,7 @@ WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlappi
 # neighbour table outside the dense tiles): ncu on the default command,
 # full-grid launches of all four solvers (see
 # profiles/step_kernels_channel_256x256x512_dram.txt)
-MEASURED_DRAM_B_PER_FLUP = {"even": 155.2, "odd": 181.3}
+MEASURED_DRAM_B_PER_FLUP = {"even": 155.1, "odd": 181.3}
 # the same for the 64 batched REV cubes (table-only odd step,
 # profiles/step_kernels_rev_64cubes_dram.txt)
 MEASURED_DRAM_B_PER_FLUP_REV = {"even": 158.5, "odd": 226.8}
