@@ -171,31 +171,6 @@ __device__ __forceinline__ void load_links(float a[kQ], uint32_t m, const float 
     }
 }
 
-// Shared-memory staged variants (a_s[k-1][t] holds the coefficient of link k
-// of thread t; each thread touches only its own column).
-__device__ __forceinline__ void stage_links(float (*a_s)[kBlock], int t, uint32_t m,
-                                            const float *__restrict__ link_a, uint32_t off)
-{
-#pragma unroll
-    for (int k = 1; k < kQ; ++k) {
-        float v = 0.0f;
-        if ((m >> k) & 1u) v = link_a[off++];
-        a_s[k - 1][t] = v;
-    }
-}
-
-__device__ __forceinline__ void cli_incoming_s(float h[kQ], const float (*a_s)[kBlock], int t)
-{
-#pragma unroll
-    for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(a_s[k - 1][t], h[k], h[opp(k)]);
-}
-
-__device__ __forceinline__ void cli_outgoing_s(float h[kQ], const float (*a_s)[kBlock], int t)
-{
-#pragma unroll
-    for (int k = 1; k < kQ; ++k) h[k] = fmaf(-a_s[k - 1][t], h[opp(k)], h[k]);
-}
-
 // Completes the incoming populations of link-reverse directions:
 // f_kbar = P + a_k f_k.  If a_k != 0 then opp(k) is no link, so the order of
 // the updates does not matter.

@@ -19,13 +19,14 @@ namespace lbm {
 namespace {
 
 // Resident blocks per SM requested from the register allocator (256 threads
-// each).  Measured on GB300 over the 256x256x512 channel sweep: the even step
-// (no shared memory) reaches 93% of the copy bandwidth at 6 blocks (40
-// registers, no spills; 7 spills); the odd step is best at 5 (48 registers,
-// 180 KB of staging per SM): at 6 its staging leaves too little L1 for the
-// neighbour gathers, which hit L1 about a third of the time.
+// each).  Measured on GB300 over the 256x256x512 channel sweep: both steps at
+// 6 blocks (40 registers, no spills; 7 blocks spill).  The odd step stages
+// only its neighbour slots in shared memory (18 KB per block) and reads the
+// CLI coefficients where it uses them, as the even step does: 10% faster
+// than also staging the coefficients at 5 blocks (48 registers, 36 KB per
+// block), which left too little L1 for the gathers.
 constexpr int kEvenBlocksPerSM = 6;
-constexpr int kOddBlocksPerSM = 5;
+constexpr int kOddBlocksPerSM = 6;
 
 // Where the odd step takes a cell's neighbour indices from: the table, the
 // row bitmasks, or the table except in dense tiles (Solver::tile_desc), whose
@@ -100,21 +101,17 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
     for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
 }
 
-// Odd step: per-thread staging in shared memory.  The CLI coefficients and
-// the neighbour indices of a thread are written and read by that thread only,
-// so no barrier is needed.  Keeping them out of registers across the
-// collision lowers register pressure and raises the number of resident warps,
-// which is what hides the memory latency of the two dependent loads (indices,
-// then populations).
+// Odd step: per-thread staging of the neighbour slots in shared memory (each
+// thread writes and reads its own column, so no barrier is needed).  Keeping
+// them out of registers across the collision lowers register pressure and
+// raises the number of resident warps, which is what hides the memory latency
+// of the two dependent loads (indices, then populations).  The CLI
+// coefficients are read where they are used, before and after the collision
+// (the second read hits L1).
 // NB: where the neighbour indices come from (NbSource).
 template <typename T, int NB>
-__device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock],
-                                         float (*a_s)[kBlock])
+__device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock])
 {
-    // resolving the slots once saves instructions, which is what limits the
-    // 16-bit kernels; in FP32 the table kernel was measured 1.6% faster
-    // resolving them at each use (periodic REV cubes, the same box)
-    constexpr bool kOnce = sizeof(T) == 2;
     const int t = threadIdx.x;
     const bool live = i < p.n_fluid;
     // 32-bit element offsets (19 n_pad < 2^32 is checked on the host)
@@ -128,32 +125,34 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
         int32_t nb[kQ];
         if (d.x >= 0) dense_neighbours(nb, d, i);
         else m = NB == kNbRows ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
-        // kOnce: stage the slot of direction k, A[k][x + e_k] or the dead slot
-        // A[opp k][x] of a wall link, which the gather of h_opp(k) reads and
-        // the scatter of the new h_k writes (the AA pattern); otherwise stage
-        // the index and resolve the slot at each use
+        // stage the slot of direction k, A[k][x + e_k] or the dead slot
+        // A[opp k][x] of a wall link: the gather of h_opp(k) reads it and the
+        // scatter of the new h_k writes it (the AA pattern), so it is
+        // resolved once
 #pragma unroll
         for (int k = 1; k < kQ; ++k)
-            nb_s[k - 1][t] = kOnce ? (int32_t)(nb[k] >= 0 ? k * n_pad + (uint32_t)nb[k] : opp(k) * n_pad + ui) : nb[k];
+            nb_s[k - 1][t] = (int32_t)(nb[k] >= 0 ? k * n_pad + (uint32_t)nb[k] : opp(k) * n_pad + ui);
     }
     // skip the link-offset scan in link-free warps only where such warps
-    // exist (solvers with dense tiles): measured 1.2% faster on the channel,
-    // 2.8% slower on the periodic REV cubes, where nearly every warp has links
+    // exist (solvers with dense tiles): measured faster on the channel and
+    // 0.8% slower on the periodic REV cubes, where nearly every warp has links
     const uint32_t off = first_link<NB == kNbDense>(p.warp_off, i, m);
     if (!live) return;
-    if (m) stage_links(a_s, t, m, p.link_a, off);
-    auto slot = [&](int k) -> uint32_t {   // slot of direction k
-        const int32_t v = nb_s[k - 1][t];
-        return kOnce ? (uint32_t)v : (v >= 0 ? k * n_pad + (uint32_t)v : opp(k) * n_pad + ui);
-    };
+    auto slot = [&](int k) -> uint32_t { return (uint32_t)nb_s[k - 1][t]; };   // slot of direction k
     float h[kQ];
     h[0] = ld_raw(p.pdf + ui);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) h[k] = ld_raw(p.pdf + slot(opp(k)));   // A[opp k][x - e_k]
-    if (m) cli_incoming_s(h, a_s, t);
+    if (m) {
+#pragma unroll
+        for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(link_coef(p.link_a, off, m, k), h[k], h[opp(k)]);
+    }
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
-    if (m) cli_outgoing_s(h, a_s, t);
+    if (m) {
+#pragma unroll
+        for (int k = 1; k < kQ; ++k) h[k] = fmaf(-link_coef(p.link_a, off, m, k), h[opp(k)], h[k]);
+    }
     st_raw(p.pdf + ui, h[0]);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) st_raw(p.pdf + slot(k), h[k]);
@@ -247,9 +246,8 @@ template <typename T, int NB, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
 {
     __shared__ int32_t nb_s[kQ - 1][kBlock];
-    __shared__ float a_s[kQ - 1][kBlock];
     for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x)
-        odd_cell<T, NB>(p, tile * kBlock + threadIdx.x, nb_s, a_s);
+        odd_cell<T, NB>(p, tile * kBlock + threadIdx.x, nb_s);
 }
 
 // Initial state f_k = f_k^eq(rho = 1, u0) (Eq. (equilibrium)) stored shifted
