@@ -116,15 +116,9 @@ static int bins_extent(const std::vector<const Geometry *> &geoms, size_t &n_bin
 {
     n_bins = 0;
     n_images = 0;
-    try {
-        for (const Geometry *g : geoms) {
-            Bins bins;
-            build_bins(g->box, g->spheres, bins);
-            n_bins = std::max(n_bins, bins.start.size() - 1);
-            n_images = std::max(n_images, bins.images.size());
-        }
-    } catch (const std::bad_alloc &) {
-        return LBM_ENOMEM;
+    for (const Geometry *g : geoms) {
+        n_bins = std::max(n_bins, g->link_bins.start.size() - 1);
+        n_images = std::max(n_images, g->link_bins.images.size());
     }
     return LBM_OK;
 }
@@ -261,6 +255,7 @@ int lbm_geometry_from_spheres(const lbm_sphere_params *params, lbm_geometry **ou
     int rc;
     try {
         rc = place_and_voxelise(*params, *g);
+        if (rc == LBM_OK) build_bins(g->box, g->spheres, g->link_bins);
     } catch (const std::bad_alloc &) {
         rc = LBM_ENOMEM;
     }
@@ -281,6 +276,7 @@ int lbm_geometry_from_list(const lbm_box *box, const double *xyzr, int64_t n, lb
     int rc;
     try {
         rc = voxelise_list(*box, xyzr, n, *g);
+        if (rc == LBM_OK) build_bins(g->box, g->spheres, g->link_bins);
     } catch (const std::bad_alloc &) {
         rc = LBM_ENOMEM;
     }

@@ -179,7 +179,9 @@ __device__ double sphere_entry(double dx, double dy, double dz, int kx, int ky, 
                                __dmul_rn(r, r));
     const double disc = __dsub_rn(__dmul_rn(B, B), __dmul_rn(A, C));
     if (!(B < 0.0) || disc < 0.0) return 2.0;
-    const double s = __ddiv_rn(__dsub_rn(-B, __dsqrt_rn(disc)), A);
+    // A = e.e is 1 or 2, so the division is exact as a multiplication by 1
+    // or 1/2 (same bits, no FP64 division)
+    const double s = __dmul_rn(__dsub_rn(-B, __dsqrt_rn(disc)), A == 1.0 ? 1.0 : 0.5);
     return s <= 1.0 ? s : 2.0;
 }
 
@@ -201,27 +203,52 @@ struct LinkArgs {
 };
 
 // 5. link fractions and CLI coefficients of the cells of one part.  The grid
-// covers the aligned groups of 32 that contain the part, so the warp prefix
-// sum of link counts sees every cell of each group.
+// covers the aligned groups of 32 that contain the part; a warp owns the
+// links of its 32 cells (stored contiguously from warp_off, cell by cell, in
+// increasing k) and processes them 32 at a time, one link per lane: the lane
+// finds the link's cell by a binary search over the warp's inclusive prefix
+// sum of link counts and its direction as the r-th set bit of that cell's
+// link mask.  (One cell per lane would run the candidate loop for every
+// direction in which any lane of the warp has a link.)
 __global__ void k_links(LinkArgs a)
 {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int32_t i = (a.begin & ~31) + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
+    const int32_t i0 = i - lane;   // first cell of the warp's group
     const uint32_t m = i < a.n_fluid ? a.lmask[i] : 0u;
     const uint32_t cnt = __popc(m);
     uint32_t incl = cnt;
-    const int lane = threadIdx.x & 31;
     for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        const uint32_t y = __shfl_up_sync(kAll, incl, d);
         if (lane >= d) incl += y;
     }
-    if (i < a.begin || i >= a.end || m == 0) return;
-    uint32_t off = a.warp_off[i >> 5] + incl - cnt;
-    const int32_t c = (int32_t)(a.fluid_cell[i] - a.cell_base);
-    const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
-    const int bin = x / kBinEdge + a.nbx * (y / kBinEdge + a.nby * (z / kBinEdge));
-    const int b0 = a.bin_start[bin], b1 = a.bin_start[bin + 1];
-    for (int k = 1; k < kQ; ++k) {
-        if (!((m >> k) & 1u)) continue;
+    const uint32_t total = __shfl_sync(kAll, incl, 31);
+    if (total == 0) return;   // warp-uniform
+    const uint32_t wbase = a.warp_off[i0 >> 5];
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t l = base + (uint32_t)lane;   // this lane's link, relative to wbase
+        // owner: the first lane whose inclusive count exceeds l
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t v = __shfl_sync(kAll, incl, lo + step - 1);
+            if (v <= l) lo += step;
+        }
+        const int j = lo < 31 ? lo : 31;
+        const uint32_t mj = __shfl_sync(kAll, m, j);
+        const uint32_t excl = __shfl_sync(kAll, incl, j) - __popc(mj);
+        const int32_t c_i = i0 + j;
+        if (l >= total || c_i < a.begin || c_i >= a.end) continue;
+        // direction: the (l - excl)-th set bit of mj (0 <= l - excl < popc(mj),
+        // since incl[j-1] <= l < incl[j])
+        uint32_t mm = mj;
+        for (uint32_t r = l - excl; r > 0; --r) mm &= mm - 1u;
+        const int k = __ffs(mm) - 1;
+        const int32_t c = (int32_t)(a.fluid_cell[c_i] - a.cell_base);
+        const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+        const int bin = x / kBinEdge + a.nbx * (y / kBinEdge + a.nby * (z / kBinEdge));
+        const int b0 = a.bin_start[bin], b1 = a.bin_start[bin + 1];
         const int kx = ex(k), ky = ey(k), kz = ez(k);
         double q = 2.0;
         if (!a.periodic_z) {
@@ -244,15 +271,14 @@ __global__ void k_links(LinkArgs a)
         // wall node on the link's line (x - 2 e_k solid), or when the wall is
         // within kCliQmin of the node: Eq. (CLI) grows without bound in such
         // sharp corners of overlapping packings
-        bool fallback = a.simple_bounce_back || ((m >> opp(k)) & 1u) || q < kCliQmin;
+        bool fallback = a.simple_bounce_back || ((mj >> opp(k)) & 1u) || q < kCliQmin;
         if (!fallback) {
-            const int32_t x2 = a.nbr[(size_t)(opp(k) - 1) * a.n_pad + i];
+            const int32_t x2 = a.nbr[(size_t)(opp(k) - 1) * a.n_pad + c_i];
             fallback = (a.lmask[x2] >> opp(k)) & 1u;
         }
         const double coef = fallback ? 0.0 : __ddiv_rn(__dsub_rn(1.0, __dmul_rn(2.0, q)), __dadd_rn(1.0, __dmul_rn(2.0, q)));
-        a.link_q[off] = q;
-        a.link_a[off] = (float)coef;
-        ++off;
+        a.link_q[wbase + l] = q;
+        a.link_a[wbase + l] = (float)coef;
     }
 }
 
@@ -361,12 +387,7 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     for (size_t b = 0; b < s.parts.size(); ++b) {
         const Part &P = s.parts[b];
         if (P.n_links == 0) continue;
-        Bins bins;
-        try {
-            build_bins(P.box, geoms[b]->spheres, bins);
-        } catch (const std::bad_alloc &) {
-            return LBM_ENOMEM;
-        }
+        const Bins &bins = geoms[b]->link_bins;
         LBM_CUDA_TRY(cudaMemcpyAsync(d_bstart, bins.start.data(), bins.start.size() * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, st));
         if (!bins.images.empty())

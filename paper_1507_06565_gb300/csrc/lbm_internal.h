@@ -70,6 +70,13 @@ struct SphereImage {
 };
 
 // Host geometry behind the lbm_geometry handle.
+// Sphere images binned on a grid of kBinEdge^3 cells (host build, device use).
+struct Bins {
+    int nbx = 0, nby = 0, nbz = 0;
+    std::vector<int32_t> start;          // [nbins+1]
+    std::vector<SphereImage> images;
+};
+
 struct Geometry {
     lbm_box box{};
     std::vector<double> spheres;   // [n][4]
@@ -77,14 +84,8 @@ struct Geometry {
     int64_t n_fluid = 0;
     int64_t n_links = 0;
     double porosity = 1.0;
+    Bins link_bins;                // the bins of the link fractions, built with the geometry
     int64_t ncell() const { return (int64_t)box.nx * box.ny * box.nz; }
-};
-
-// Sphere images binned on a grid of kBinEdge^3 cells (host build, device use).
-struct Bins {
-    int nbx = 0, nby = 0, nbz = 0;
-    std::vector<int32_t> start;          // [nbins+1]
-    std::vector<SphereImage> images;
 };
 
 // One independent box of a solver.  A solver advances the union of its parts
