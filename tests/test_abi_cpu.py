@@ -93,3 +93,29 @@ def test_error_codes(lib):
         L.lbm_workspace_size(geom, L.make_params(tau=0.5))
     assert e.value.status == L.LBM_EINVAL
     assert L.lbm_workspace_size(geom, L.make_params()) > 0
+
+
+def test_flags_validated_on_host(lib):
+    """Every documented LBM_FLAG_* value (and the allowed combinations) is
+    accepted by the host-side size query; undefined bits and the two
+    neighbour variants together are refused."""
+    geom = L.lbm_geometry_from_list(8, 8, 8, False, [[4.0, 4.0, 4.0, 2.0]])
+    base = L.lbm_workspace_size(geom, L.make_params())
+    for f in (L.LBM_FLAG_NEIGHBOUR_TABLE, L.LBM_FLAG_ROW_NEIGHBOURS, L.LBM_FLAG_NO_GRAPH, L.LBM_FLAG_NO_AUTOTUNE,
+              L.LBM_FLAG_SIMPLE_BOUNCE_BACK, L.LBM_FLAG_STAGED_EVEN,
+              L.LBM_FLAG_STAGED_EVEN | L.LBM_FLAG_NO_AUTOTUNE | L.LBM_FLAG_NEIGHBOUR_TABLE):
+        assert L.lbm_workspace_size(geom, L.make_params(flags=f)) == base
+    for f in (16, 128, 1 << 20, L.LBM_FLAG_NEIGHBOUR_TABLE | L.LBM_FLAG_ROW_NEIGHBOURS):
+        with pytest.raises(L.LBMError) as e:
+            L.lbm_workspace_size(geom, L.make_params(flags=f))
+        assert e.value.status == L.LBM_EINVAL
+
+
+def test_geometry_keeps_its_sphere_bins(lib):
+    """The link bins are part of the geometry: repeated size queries agree,
+    and two geometries from the same spheres give the same sizes."""
+    sp = [[5.25, 4.5, 3.0, 2.5], [-0.5, 0.25, 6.0, 1.75]]
+    a = L.lbm_geometry_from_list(10, 9, 12, False, sp)
+    b = L.lbm_geometry_from_list(10, 9, 12, False, sp)
+    p = L.make_params()
+    assert L.lbm_workspace_size(a, p) == L.lbm_workspace_size(a, p) == L.lbm_workspace_size(b, p)
