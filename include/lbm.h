@@ -95,12 +95,14 @@ typedef struct {
 } lbm_sphere_params;
 
 /* Variant of the odd (gather/scatter) step; both address the same slots and
- * differ only in FP32 rounding.  LBM_FLAG_NEIGHBOUR_TABLE reads the 18 neighbour indices of a cell
+ * give the same bits.  LBM_FLAG_NEIGHBOUR_TABLE reads the 18 neighbour indices of a cell
  * from the stored table (72 bytes per cell and odd step);
  * LBM_FLAG_ROW_NEIGHBOURS computes them from per-row fluid bitmasks (about
  * 4 bytes per cell, but two dependent loads before the gathers).  Neither:
- * the table, which measured faster for every storage type.  The table is also
- * used whenever ny*nz does not fit beside x in 32 bits. */
+ * the table, which measured faster for every storage type, with computed
+ * indices in tiles of 256 cells whose planes and neighbour planes are all
+ * fluid.  The table is also used whenever ny*nz does not fit beside x in
+ * 32 bits. */
 #define LBM_FLAG_NEIGHBOUR_TABLE 1
 #define LBM_FLAG_ROW_NEIGHBOURS 2
 /* Scheduling switches.  By default lbm_step times a few grid sizes for each
