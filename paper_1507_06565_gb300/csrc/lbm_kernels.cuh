@@ -154,11 +154,22 @@ __device__ __forceinline__ uint32_t first_link(const uint32_t *__restrict__ warp
     return warp_off[i >> 5] + incl - cnt;
 }
 
-// CLI coefficient of direction k (0 unless k is a link of mask m): the links of
-// a cell are stored in increasing k from its first link `off`.
-__device__ __forceinline__ float link_coef(const float *__restrict__ link_a, uint32_t off, uint32_t m, int k)
+// Eq. (CLI) on the links of mask m, whose coefficients are stored from off in
+// increasing k: before the collision (INCOMING) the incoming populations are
+// completed, h_opp(k) += a_k h_k; after it the partials are formed,
+// h_k -= a_k h_opp(k).  A running index over the set bits replaces a
+// popcount per direction; directions without a link are left untouched.
+template <bool INCOMING>
+__device__ __forceinline__ void cli_links(float h[kQ], const float *__restrict__ link_a, uint32_t off, uint32_t m)
 {
-    return ((m >> k) & 1u) ? link_a[off + __popc(m & ((1u << k) - 1u))] : 0.0f;
+    uint32_t r = off;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k)
+        if ((m >> k) & 1u) {
+            const float a = link_a[r++];
+            if (INCOMING) h[opp(k)] = fmaf(a, h[k], h[opp(k)]);
+            else h[k] = fmaf(-a, h[opp(k)], h[k]);
+        }
 }
 
 // CLI coefficients a[k] of the links in m (0 elsewhere).

@@ -87,16 +87,10 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
     float h[kQ];
 #pragma unroll
     for (int k = 0; k < kQ; ++k) h[k] = ld_raw(p.pdf + k * n_pad + i);
-    if (m) {
-#pragma unroll
-        for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(link_coef(p.link_a, off, m, k), h[k], h[opp(k)]);
-    }
+    if (m) cli_links<true>(h, p.link_a, off, m);
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
-    if (m) {
-#pragma unroll
-        for (int k = 1; k < kQ; ++k) h[k] = fmaf(-link_coef(p.link_a, off, m, k), h[opp(k)], h[k]);
-    }
+    if (m) cli_links<false>(h, p.link_a, off, m);
 #pragma unroll
     for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
 }
@@ -143,16 +137,10 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     h[0] = ld_raw(p.pdf + ui);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) h[k] = ld_raw(p.pdf + slot(opp(k)));   // A[opp k][x - e_k]
-    if (m) {
-#pragma unroll
-        for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(link_coef(p.link_a, off, m, k), h[k], h[opp(k)]);
-    }
+    if (m) cli_links<true>(h, p.link_a, off, m);
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
-    if (m) {
-#pragma unroll
-        for (int k = 1; k < kQ; ++k) h[k] = fmaf(-link_coef(p.link_a, off, m, k), h[opp(k)], h[k]);
-    }
+    if (m) cli_links<false>(h, p.link_a, off, m);
     st_raw(p.pdf + ui, h[0]);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) st_raw(p.pdf + slot(k), h[k]);
@@ -223,16 +211,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
         if (__syncthreads_or(!ok)) break;   // the stage is free again
         if (t < 32 && j + S < count) issue(j + S);
         if (!live) continue;
-        if (m) {
-#pragma unroll
-            for (int k = 1; k < kQ; ++k) h[opp(k)] = fmaf(link_coef(p.link_a, off, m, k), h[k], h[opp(k)]);
-        }
+        if (m) cli_links<true>(h, p.link_a, off, m);
         if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
         collide(h, p.c);
-        if (m) {
-#pragma unroll
-            for (int k = 1; k < kQ; ++k) h[k] = fmaf(-link_coef(p.link_a, off, m, k), h[opp(k)], h[k]);
-        }
+        if (m) cli_links<false>(h, p.link_a, off, m);
 #pragma unroll
         for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
     }
