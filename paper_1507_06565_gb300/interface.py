@@ -124,3 +124,38 @@ def profile_otw(z, z_int, z_top, K, nu, nu_eff, g, beta):
     b = np.array([0.5 * g / nu * L * L - u_m, beta * nu / np.sqrt(K) * u_m])
     A, du = np.linalg.solve(M, b)
     return np.where(z >= z_int, _free(z, z_int, u_m + A, du, g, nu), u_m + A * np.exp(r * (z - z_int)))
+
+
+def profile_brinkman_layer(z, z_bot, z_int, z_top, K, eps, nu, g, nu_eff=None):
+    """Single-domain Brinkman profile of a channel with a porous layer
+    (Eq. (Br) with the drag of Eq. (PorousForce), Stokes regime): in the
+    porous layer z_bot < z < z_int
+
+        nu_eff u'' - (eps nu / K) u + eps g = 0,
+
+    in the free layer z_int < z < z_top  nu u'' + g = 0; no slip at the walls
+    z_bot and z_top; u and the shear stress (nu_eff u' below, nu u' above)
+    continuous at z_int.  u is the superficial velocity; nu_eff defaults to
+    nu / eps (Sec. 4's choice).  The porous solution is the Darcy velocity
+    g K / nu plus exponentials of rate r = sqrt(eps nu / (K nu_eff)), written
+    as e^{r (z - z_int)} and e^{-r (z - z_bot)} so that both stay <= 1 in the
+    layer and the 4 x 4 system for their amplitudes and the free parabola's
+    two coefficients stays well conditioned."""
+    z = np.asarray(z, float)
+    nu_e = nu / eps if nu_eff is None else nu_eff
+    r = np.sqrt(eps * nu / (K * nu_e))
+    u_d = g * K / nu
+    H = z_int - z_bot
+    Lf = z_top - z_int
+    e_h = np.exp(-r * H)
+    # unknowns A, B (porous), C, D (free: u = -g/(2 nu) s^2 + C s + D, s = z - z_int)
+    M = np.array([[e_h, 1.0, 0.0, 0.0],                    # u(z_bot) = 0
+                  [0.0, 0.0, Lf, 1.0],                     # u(z_top) = 0
+                  [1.0, e_h, 0.0, -1.0],                   # u continuous at z_int
+                  [nu_e * r, -nu_e * r * e_h, -nu, 0.0]])  # stress continuous at z_int
+    b = np.array([-u_d, 0.5 * g / nu * Lf * Lf, -u_d, 0.0])
+    A, B, C, D = np.linalg.solve(M, b)
+    s = z - z_int
+    porous = u_d + A * np.exp(r * np.minimum(s, 0.0)) + B * np.exp(-r * np.maximum(z - z_bot, 0.0))
+    free = -0.5 * g / nu * s * s + C * s + D
+    return np.where(z >= z_int, free, porous)

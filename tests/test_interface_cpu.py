@@ -60,3 +60,46 @@ def test_interface_position():
     eps = np.concatenate([np.full(100, 0.6), [0.8, 0.95], np.ones(50)])
     z = np.arange(eps.size, dtype=float)
     assert I.interface_position(z, eps) == 102.0
+
+
+@pytest.mark.parametrize("K,eps", [(3.0, 0.6), (0.4, 0.35), (25.0, 0.9)])
+def test_brinkman_layer_profile_satisfies_its_problem(K, eps):
+    """The two-layer Brinkman profile solves its ODEs (second differences on
+    a fine grid), meets both walls, and is continuous in u and in stress
+    (nu_eff u' = nu u') at the interface."""
+    nu, g = 0.1, 1e-6
+    zb, zi, zt = 0.5, 40.0, 80.0
+    nu_e = nu / eps
+    u = lambda z: I.profile_brinkman_layer(z, zb, zi, zt, K, eps, nu, g)
+    h = 1e-3
+    for z in np.linspace(zb + 0.5, zi - 0.5, 7):
+        d2 = (u(z + h) - 2 * u(z) + u(z - h)) / h ** 2
+        assert abs(nu_e * d2 - eps * nu / K * u(z) + eps * g) < 1e-6 * eps * g
+    for z in np.linspace(zi + 0.5, zt - 0.5, 7):
+        d2 = (u(z + h) - 2 * u(z) + u(z - h)) / h ** 2
+        assert abs(nu * d2 + g) < 1e-6 * g
+    umax = float(np.max(u(np.linspace(zb, zt, 801))))
+    assert abs(float(u(zb))) < 1e-12 * umax and abs(float(u(zt))) < 1e-12 * umax
+    d = 1e-7
+    assert abs(float(u(zi - d)) - float(u(zi + d))) < 1e-6 * umax
+    # second-order one-sided differences on each side of the interface
+    a, b = zi - d, zi + d
+    s_below = nu_e * (3 * float(u(a)) - 4 * float(u(a - h)) + float(u(a - 2 * h))) / (2 * h)
+    s_above = nu * (-3 * float(u(b)) + 4 * float(u(b + h)) - float(u(b + 2 * h))) / (2 * h)
+    assert abs(s_below - s_above) < 1e-5 * abs(s_above)
+
+
+def test_brinkman_layer_limits():
+    """No drag (K -> infinity, eps = 1, nu_eff = nu): plane Poiseuille flow
+    between the walls.  Vanishing permeability: the porous layer is at rest
+    and the free layer is Poiseuille flow between the interface and the top
+    wall."""
+    nu, g = 0.1, 1e-6
+    zb, zi, zt = 0.5, 30.0, 70.0
+    z = np.linspace(zb, zt, 281)
+    u = I.profile_brinkman_layer(z, zb, zi, zt, 1e12, 1.0, nu, g, nu_eff=nu)
+    want = 0.5 * g / nu * (z - zb) * (zt - z)
+    assert np.max(np.abs(u - want)) < 1e-6 * np.max(want)
+    u0 = I.profile_brinkman_layer(z, zb, zi, zt, 1e-10, 0.5, nu, g)
+    want0 = np.where(z >= zi, 0.5 * g / nu * (z - zi) * (zt - z), 0.0)
+    assert np.max(np.abs(u0 - want0)) < 1e-4 * np.max(want0)

@@ -514,3 +514,66 @@ def test_binned_link_search_equals_exhaustive():
     b = O.build_lists(*box, False, sp, q_lo=0.4, q_hi=0.6, use_bins=True)
     for key in a:
         assert np.array_equal(a[key], b[key]), key
+
+
+def test_tiny_lattice_steady_state_direct_solve():
+    """Brute force on a 4x4x6 box (walls z = 0, 5; one sphere; bounce-back on
+    every link): with a force small enough that the quadratic equilibrium
+    terms are ~1e-6 of the flow, one step is an affine map f -> M f + b.  M
+    and b are assembled here from the definitions -- TRT relaxation of the
+    symmetric and antisymmetric parts towards the linear equilibrium
+    w_k (rho + 3 e_k.j), the source 3 w_k e_k.g, periodic streaming in x and
+    y, half-way bounce-back into the solid -- and the steady state (I - M) f
+    = b with the total mass fixed (bounce-back conserves it) is solved
+    directly.  The oracle, iterated from rest, must reach that state: its
+    iterate keeps an undamped period-2 component (M has eigenvalues -1 as well
+    as the mass mode +1 here), so the mean of two consecutive iterates is the
+    fixed point."""
+    nx, ny, nz = 4, 4, 6
+    sp = [[1.7, 2.2, 2.6, 1.2]]
+    tau, lam = 0.8, 3.0 / 16.0
+    # u ~ 1e-6: the quadratic equilibrium terms are ~1e-6 of the flow, and
+    # FP64 rounding accumulated in the lattice's undamped modes (~1e-12
+    # absolute over the iterations) stays below 1e-5 of it
+    g = np.array([1.5e-7, 0.6e-7, 0.0])
+    lat = O.Lattice(nx, ny, nz, False, sp, tau, lam, tuple(g), simple_bounce_back=True).init()
+    solid = lat.solid().astype(bool)
+    fluid = np.argwhere(~solid)              # (z, y, x), x fastest
+    nf = len(fluid)
+    assert 0 < nf < nx * ny * (nz - 2)       # the sphere cuts some cells
+    idx = -np.ones(solid.shape, int)
+    idx[tuple(fluid.T)] = np.arange(nf)
+    e, w = O.velocity_set()
+    E = e.astype(float)
+    opp = [O.opposite(k) for k in range(19)]
+    w_plus = 1.0 / tau
+    w_minus = 1.0 / (lam / (tau - 0.5) + 0.5)
+    I19 = np.eye(19)
+    Peq = w[:, None] * (1.0 + 3.0 * E @ E.T)     # f^eq = Peq f (linear part)
+    Pk = I19[opp]                                # (Pk f)_k = f_opp(k)
+    sym, anti = 0.5 * (I19 + Pk), 0.5 * (I19 - Pk)
+    C = I19 - w_plus * sym @ (I19 - Peq) - w_minus * anti @ (I19 - Peq)
+    src = 3.0 * w * (E @ g)
+    n = 19 * nf
+    M = np.zeros((n, n))
+    b = np.zeros(n)
+    for c, (z, y, x) in enumerate(fluid):
+        for k in range(19):
+            zn, yn, xn = z + e[k, 2], (y + e[k, 1]) % ny, (x + e[k, 0]) % nx
+            dst = 19 * idx[zn, yn, xn] + k if not solid[zn, yn, xn] else 19 * c + opp[k]
+            M[dst, 19 * c:19 * c + 19] += C[k]
+            b[dst] += src[k]
+    lat.step(4000)   # the slowest decaying mode has |lambda| ~ 0.967
+    f_a = lat.get_f()[:, fluid[:, 0], fluid[:, 1], fluid[:, 2]].T
+    lat.step(1)
+    f_b = lat.get_f()[:, fluid[:, 0], fluid[:, 1], fluid[:, 2]].T
+    f = 0.5 * (f_a + f_b)
+    A = np.vstack([np.eye(n) - M, np.ones((1, n))])
+    # the oracle's mass (rounding moves it by ~1e-14 per step; bounce-back keeps it otherwise)
+    f_star = np.linalg.lstsq(A, np.concatenate([b, [f.sum()]]), rcond=None)[0].reshape(nf, 19)
+    assert abs(f.sum() - nf) < 1e-8
+    dev_star = f_star - w
+    assert np.max(np.abs(dev_star)) > 1e-8                       # a non-trivial flow
+    assert np.max(np.abs(f - f_star)) <= 2e-5 * np.max(np.abs(dev_star))
+    j_star, j = f_star @ E, f @ E
+    assert np.max(np.abs(j - j_star)) <= 2e-6 * np.max(np.abs(j_star))
