@@ -316,7 +316,7 @@ int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int3
 
 /* Shifted populations h_k = f_k - w_k of the current state (the streamed
  * populations of Eq. (streaming) at the current time) into the device buffer
- * dev_out[19][n_fluid] (float).  Asynchronous. */
+ * dev_out[19][n_fluid] (float; may be NULL when n_fluid is 0).  Asynchronous. */
 int lbm_populations(lbm_solver *solver, float *dev_out);
 
 /* Plane averages without any device allocation (the paper has no

@@ -670,7 +670,9 @@ int lbm_export_lists(lbm_solver *s, int32_t *fluid_cell, int32_t *nbr, int32_t *
 
 int lbm_populations(lbm_solver *s, float *dev_out)
 {
-    if (!s || !dev_out) return LBM_EINVAL;
+    if (!s) return LBM_EINVAL;
+    if (s->n_fluid == 0) return LBM_OK;   // nothing to write
+    if (!dev_out) return LBM_EINVAL;
     return launch_populations(*s, dev_out);
 }
 

@@ -119,3 +119,17 @@ def test_geometry_keeps_its_sphere_bins(lib):
     b = L.lbm_geometry_from_list(10, 9, 12, False, sp)
     p = L.make_params()
     assert L.lbm_workspace_size(a, p) == L.lbm_workspace_size(a, p) == L.lbm_workspace_size(b, p)
+
+
+def test_size_limit_of_32bit_slot_offsets(lib):
+    """The step kernels address population slots with 32-bit offsets, so a
+    solver takes at most 2^32 / 19 padded fluid cells (~226 M): a 624^3
+    channel (242 M fluid cells) is refused, a 600^3 one (215 M) accepted."""
+    big = L.lbm_geometry_from_list(624, 624, 624, False, [])
+    assert big.info()["n_fluid"] * 19 > 2 ** 32
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_workspace_size(big, L.make_params())
+    assert e.value.status == L.LBM_EINVAL
+    del big
+    ok = L.lbm_workspace_size(L.lbm_geometry_from_list(600, 600, 600, False, []), L.make_params())
+    assert ok > 600 * 600 * 598 * 19 * 4

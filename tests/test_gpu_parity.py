@@ -306,6 +306,46 @@ def test_staged_even_step_bit_exact(torch_cuda, storage, case):
     a.residual()   # synchronises and reads the kernels' timeout word (LBMError if set)
 
 
+def test_geometry_without_fluid(torch_cuda):
+    """Degenerate input: a walled 8 x 8 x 4 box whose two fluid planes four
+    overlapping spheres fill has no fluid cell.  The solver builds, steps
+    (both parities) and reports empty fields without launching empty grids."""
+    spheres = [[x, y, 1.5, 3.0] for x in (1.5, 5.5) for y in (1.5, 5.5)]
+    geom = L.lbm_geometry_from_list(8, 8, 4, False, spheres)
+    assert geom.info()["n_fluid"] == 0
+    solver = L.Solver(geom, g=(1e-5, 0, 0))
+    solver.step(3)
+    assert solver.steps == 3
+    rho, u = solver.moments()
+    assert float(rho.abs().max()) == 0.0 and float(u.abs().max()) == 0.0
+    pa = solver.plane_average()
+    assert np.array_equal(pa, np.zeros_like(pa))
+    assert solver.populations().numel() == 0
+
+
+@pytest.mark.parametrize("q", [(0.5, 0.5), (0.3, 0.8)])
+def test_one_cell_wide_column(torch_cuda, q):
+    """Degenerate box: 1 x 1 x 18 with walls, so every x and y neighbour of a
+    cell is the cell itself (periodic wrap onto itself) and the 16 fluid
+    cells fill one ragged tile.  Every population after both parities and
+    after 300 steps against the oracle, on half-way and off-grid walls."""
+    import torch
+
+    g = (2e-5, 1e-5, 0.0)
+    geom = L.lbm_geometry_from_list(1, 1, 18, False, [], q_lo=q[0], q_hi=q[1])
+    assert geom.info()["n_fluid"] == 16
+    u0 = W.velocity_field((18, 1, 1), seed=4, amplitude=1e-2)
+    solver = L.Solver(geom, 0.8, 3 / 16, g, u0=torch.from_numpy(u0).cuda())
+    lat = O.Lattice(1, 1, 18, False, [], 0.8, 3 / 16, g, q[0], q[1]).init(u0.astype(np.float64))
+    fluid = solver.export_lists()["fluid_cell"]
+    for n in (1, 1, 298):
+        solver.step(n)
+        lat.step(n)
+        got = solver.populations().cpu().numpy().astype(np.float64)
+        want = _oracle_shifted(lat, fluid)
+        assert np.max(np.abs(got - want)) <= TOL_U * np.max(np.abs(want)), n
+
+
 @pytest.mark.parametrize("flags", [1, 2])
 def test_odd_step_variants_agree(torch_cuda, flags):
     """Neighbour table and row-bitmask neighbours address the same slots, and
