@@ -314,6 +314,14 @@ int lbm_solver_info(const lbm_solver *solver, lbm_geometry_info *out);
 int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int32_t *link_cell,
                      int8_t *link_k, double *link_q, uint8_t *link_fallback);
 
+/* Self-test of failure detection: one warp on the solver's stream waits, with
+ * the bounded mbarrier wait of the staged step kernels, on a barrier phase
+ * that nothing completes; after max_polls polls (>= 1) it gives up and sets
+ * the solver's status word.  Synchronises and returns what the synchronising
+ * calls return after such an event: LBM_ETIMEOUT, with the word cleared and
+ * the solver usable.  Touches no populations. */
+int lbm_wait_selftest(lbm_solver *solver, int32_t max_polls);
+
 /* Shifted populations h_k = f_k - w_k of the current state (the streamed
  * populations of Eq. (streaming) at the current time) into the device buffer
  * dev_out[19][n_fluid] (float; may be NULL when n_fluid is 0).  Asynchronous. */

@@ -111,6 +111,7 @@ SIGNATURES = {
     "lbm_solver_info": (_I, [_P, ctypes.POINTER(lbm_geometry_info)]),
     "lbm_export_lists": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "lbm_populations": (_I, [_P, _P]),
+    "lbm_wait_selftest": (_I, [_P, _I32]),
     "lbm_plane_average_static": (_I, [_P, _P, _I32, _I32, _I32, _P, _P]),
     "lbm_batch_workspace_size": (_I, [_P, _I32, ctypes.POINTER(lbm_params), ctypes.POINTER(_SZ)]),
     "lbm_batch_init": (_I, [_P, _I32, ctypes.POINTER(lbm_params), _P, _SZ, _P, _P, ctypes.POINTER(_P)]),

@@ -668,6 +668,14 @@ int lbm_export_lists(lbm_solver *s, int32_t *fluid_cell, int32_t *nbr, int32_t *
     return cudaStreamSynchronize(st) == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
+int lbm_wait_selftest(lbm_solver *s, int32_t max_polls)
+{
+    if (!s || max_polls < 1) return LBM_EINVAL;
+    const int rc = launch_wait_selftest(*s, max_polls);
+    if (rc != LBM_OK) return rc;
+    return sync_checked(s);
+}
+
 int lbm_populations(lbm_solver *s, float *dev_out)
 {
     if (!s) return LBM_EINVAL;

@@ -208,6 +208,7 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms);
 // ---- step kernels (lbm_step.cu) ----
 int launch_init(Solver &s, const float *dev_u0);
 int launch_steps(Solver &s, int64_t n);
+int launch_wait_selftest(Solver &s, int max_polls);
 
 // ---- post-processing (lbm_post.cu) ----
 int launch_fluid_moments(Solver &s);                       // -> u_cur, rho_cur

@@ -107,9 +107,9 @@ __device__ __forceinline__ bool test(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, int max_polls = kMaxPolls)
 {
-    for (int it = 0; it < kMaxPolls; ++it)
+    for (int it = 0; it < max_polls; ++it)
         if (test(bar, parity)) return true;
     return false;
 }

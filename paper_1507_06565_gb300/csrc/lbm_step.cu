@@ -226,6 +226,22 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
     }
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier phase that
+// nothing completes (no arrival, no copy), gives up after max_polls polls and
+// reports it in the status word, as a step kernel whose copies never landed
+// would.  Touches only its shared barrier and the status word.
+__global__ void k_wait_selftest(int *status, int max_polls)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        bulk::init(&bar, 1);
+        bulk::fence_init();
+    }
+    __syncthreads();
+    const bool ok = bulk::wait(&bar, 0u, max_polls);
+    if (!ok && threadIdx.x == 0) atomicExch(status, 1);
+}
+
 template <typename T, int NB, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
 {
@@ -479,6 +495,12 @@ int launch_init(Solver &s, const float *dev_u0)
     case LBM_BF16: return run_init<__nv_bfloat16>(s, dev_u0);
     }
     return LBM_EINVAL;
+}
+
+int launch_wait_selftest(Solver &s, int max_polls)
+{
+    k_wait_selftest<<<1, 32, 0, s.stream>>>(s.status, max_polls);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
 int launch_steps(Solver &s, int64_t n)

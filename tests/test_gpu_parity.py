@@ -239,6 +239,24 @@ def test_nan_is_reported(torch_cuda):
     assert e.value.status == L.LBM_ENAN
 
 
+def test_bounded_wait_reports_timeout(torch_cuda):
+    """Failure detection without a fault: a bounded mbarrier wait on a phase
+    that nothing completes gives up, the status word turns into LBM_ETIMEOUT
+    at the next synchronisation, and the solver keeps working (the word is
+    cleared; the next steps and reductions succeed)."""
+    case = CASES[0]
+    solver, lat, _ = _pair(torch_cuda, case)
+    lib = L.load_library()
+    assert lib.lbm_wait_selftest(solver.handle, 0) == L.LBM_EINVAL
+    assert lib.lbm_wait_selftest(solver.handle, 4096) == L.LBM_ETIMEOUT
+    solver.step(6)
+    lat.step(6)
+    assert solver.residual() is not None   # synchronises: no stale timeout
+    _, u = solver.moments()
+    _, u_o = lat.moments()
+    assert np.max(np.abs(u.cpu().numpy() - u_o)) <= TOL_U * np.max(np.abs(u_o))
+
+
 def test_workspace_too_small(torch_cuda):
     torch = torch_cuda
     geom = L.lbm_geometry_from_spheres(*CASES[1].sphere_args())
