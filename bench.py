@@ -697,7 +697,7 @@ def run_ours(args, world, rank, local):
     # dram__bytes_write.sum, profiles/step_kernels_channel_256x256x512_dram.txt):
     # only for the configuration it was taken on
     traffic = None
-    if args.storage == "f32" and args.odd == "auto":
+    if args.storage == "f32" and args.odd == "auto" and args.even == "auto":
         if args.workload == "channel":
             traffic = float(np.mean(nfs)) * 0.5 * (MEASURED_DRAM_B_PER_FLUP["even"] + MEASURED_DRAM_B_PER_FLUP["odd"])
         elif args.workload == "rev" and args.cubes == 64:
