@@ -204,6 +204,19 @@ def workload_name(args):
             "as one batch: one launch per step for all cubes")
 
 
+# Wall rule per workload when --wall-rule is "auto": Eq. (CLI) as the paper
+# states it wherever the cli-stability sweep found every packing of the
+# workload stable, the corner safeguards (LBM_FLAG_CLI_SAFEGUARDS) elsewhere.
+STABLE_PAPER_CLI = {"channel": True, "channel-half": True, "large": True, "w0": True, "rev": False}
+
+
+def wall_rule(args) -> str:
+    rule = getattr(args, "wall_rule", "auto")
+    if rule == "auto":
+        rule = "paper" if STABLE_PAPER_CLI.get(getattr(args, "workload", "channel"), False) else "safeguards"
+    return rule
+
+
 def odd_flags(args) -> int:
     import paper_1507_06565_gb300 as L
 
@@ -213,7 +226,16 @@ def odd_flags(args) -> int:
         flags |= L.LBM_FLAG_SIMPLE_BOUNCE_BACK
     if getattr(args, "even", "auto") == "staged":
         flags |= L.LBM_FLAG_STAGED_EVEN
+    if wall_rule(args) == "safeguards":
+        flags |= L.LBM_FLAG_CLI_SAFEGUARDS
     return flags
+
+
+def fallback_fraction(solver) -> dict:
+    """Wall links of a solver and the fraction of them that take simple
+    bounce-back instead of Eq. (CLI) under its wall rule."""
+    fb = solver.link_fallback()
+    return {"links": int(fb.size), "bounce_back_fraction": float(fb.mean()) if fb.size else 0.0}
 
 
 def run_converge(args):
@@ -585,6 +607,92 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def _stability_sets():
+    """Every packing the benchmarks and studies run, grouped as solvers: name,
+    geometry builder, cases (one solver per entry; a list is one batch)."""
+    sets = [("W1 32x32x64 RSA r=4", [W.W1])]
+    sets += [(c.name, [c]) for c in (W.W2(phi) for phi in W.W2_POROSITIES)]
+    sets += [(W.W2_half(phi).name, [W.W2_half(phi)]) for phi in W.W2_POROSITIES]
+    sets.append(("W0 151^3 one sphere D=90", [W.W0]))
+    sets.append(("W4 64 REV cubes", [W.W4_cube(i) for i in range(64)]))
+    sets.append(("W5 warm-start channels 64x64x128 r=4 (seeds 500000-500015)",
+                 [W.Channel(f"warm-start channel {sd}", 64, 64, 128, 1.0, 64.0, 4.0, 4.0,
+                            float(np.random.default_rng(sd).uniform(0.6, 0.8)), True, sd) for sd in
+                  range(500000, 500016)]))
+    return sets
+
+
+def run_cli_stability(args):
+    """Stability of the wall rule on every packing: g = 0, a white-noise
+    perturbation of the rest state (velocity amplitude 1e-6 per cell), and the
+    largest |u| of each box after 2000 steps and after --stability-steps.  A
+    stable wall rule lets the perturbation decay (ratio < 1); Eq. (CLI) in a
+    corner where it is unstable makes it grow without bound.  Reports, per box,
+    the ratio, the cell of the largest |u| at the end, and the fraction of wall
+    links that take simple bounce-back."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    rows = []
+    first = 2000
+    for name, cases in _stability_sets():
+        if cases[0] is W.W0:
+            geoms = [L.lbm_geometry_from_list(*W.W0_BOX, True, W.W0_SPHERES)]
+        else:
+            geoms = [L.lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
+        cells = sum(g.info()["n_cells"] for g in geoms)
+        gen = torch.Generator(device="cuda").manual_seed(1)
+        u0 = 1e-6 * torch.randn(3 * cells, device="cuda", generator=gen)
+        kw = dict(tau=cases[0].tau, lam=cases[0].lam, g=(0.0, 0.0, 0.0), storage="f32", flags=odd_flags(args))
+        if len(geoms) > 1:
+            s = L.BatchSolver(geoms, u0=u0, **kw)
+            offs = [s.part_info(b)["cell_offset"] for b in range(len(geoms))]
+        else:
+            s = L.Solver(geoms[0], u0=u0, **kw)
+            offs = [0]
+        offs.append(cells)
+        del u0
+        links = fallback_fraction(s)
+
+        def part_max():
+            _, u = s.moments()
+            a = u.abs().amax(dim=0).reshape(-1)
+            return [(float(a[offs[b]:offs[b + 1]].max()), int(a[offs[b]:offs[b + 1]].argmax()))
+                    for b in range(len(geoms))]
+
+        t0 = time.perf_counter()
+        s.step(first)
+        m0 = part_max()
+        s.step(args.stability_steps - first)
+        m1 = part_max()
+        torch.cuda.synchronize()
+        parts = []
+        for b, c in enumerate(cases):
+            ratio = m1[b][0] / m0[b][0] if m0[b][0] > 0 else float("inf")
+            if not np.isfinite(m1[b][0]):
+                ratio = float("inf")
+            cell = m1[b][1]
+            nx, ny = geoms[b].shape[2], geoms[b].shape[1]
+            parts.append({"box": c.name, "ratio": ratio, "max_u_end": m1[b][0],
+                          "argmax_xyz": [cell % nx, (cell // nx) % ny, cell // (nx * ny)]})
+        worst = max(p["ratio"] for p in parts)
+        rows.append({"set": name, "worst_ratio": worst, "stable": bool(worst < 1.0), "unstable_boxes":
+                     [p for p in parts if not p["ratio"] < 1.0], "links": links,
+                     "seconds": time.perf_counter() - t0})
+        del s
+        torch.cuda.empty_cache()
+    line = {"metric": "growth of a rest-state perturbation under the wall rule (max|u| ratio)",
+            "value": max(r["worst_ratio"] for r in rows), "unit": "ratio", "higher_is_better": False,
+            "data": "synthetic", "config": {"wall_rule": wall_rule(args), "steps": args.stability_steps,
+                                            "first": first, "perturbation": "white noise, |u| ~ 1e-6, g = 0"},
+            "sets": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -646,6 +754,7 @@ def run_ours(args, world, rank, local):
         while not s.schedule()["tuned"] and s.steps < 256:
             s.step(2)
     schedules = [s.schedule() for s in solvers]
+    links = [fallback_fraction(s) for s in solvers]
 
     def one_step(events=None):
         for s in solvers:
@@ -683,14 +792,17 @@ def run_ours(args, world, rank, local):
     # per-launch algorithmic bytes: 19 loads + 19 stores of the stored type per fluid cell
     bytes_per_flup = 19 * 2 * (4 if args.storage == "f32" else 2)
     bytes_per_launch = np.array(nfs, dtype=np.float64) * bytes_per_flup
-    achieved = float((bytes_per_launch[None, :] / (durs * 1e-3)).mean() / 1e9)
+    # algorithmic bytes of all timed launches over their summed event time
+    # (a launch-weighted rate; the gaps between launches are in ms_per_step)
+    achieved = float(bytes_per_launch.sum() * args.steps / (durs.sum() * 1e-3) / 1e9)
+    peak, peak_kind = _peak_hbm()
     parity = {}
     for off in (0, 1):
         sel = durs[off::2]
         if sel.size:
             name = "even" if (first_parity + off) % 2 == 0 else "odd"
-            parity[name] = float((bytes_per_launch[None, :] / (sel * 1e-3)).mean() / 1e9)
-    peak, peak_kind = _peak_hbm()
+            gbs = float(bytes_per_launch.sum() * sel.shape[0] / (sel.sum() * 1e-3) / 1e9)
+            parity[name] = {"achieved": gbs, "frac": gbs / peak, "share": float(sel.sum() / durs.sum())}
     value = whole_job_rate(nf_total * args.steps, ms, world)
     # DRAM bytes per fluid cell and launch of the step kernels as they stand,
     # from one ncu capture of this command (dram__bytes_read.sum +
@@ -731,15 +843,17 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage, "odd_neighbours": args.odd, "even_step": args.even,
-                   "schedule": schedules,
+        "config": {"workload": workload_name(args), "fluid_cells": nfs, "storage": args.storage,
+                   "odd_neighbours": args.odd, "even_step": args.even, "wall_rule": wall_rule(args),
+                   "wall_links": links, "schedule": schedules,
                    "l2": "inputs larger than L2 ({:.1f}-{:.1f} GB of populations and indices per solver)".format(
                        *(n * (19 * (4 if args.storage == "f32" else 2) + 76) / 1e9 for n in (min(nfs), max(nfs)))),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_step_even/k_step_odd (fused AA stream-collide + CLI)",
-                     "bytes_per_flup": bytes_per_flup, "peak_kind": peak_kind, "by_parity": parity},
+                     "bytes_per_flup": bytes_per_flup, "peak_kind": peak_kind, "by_kernel": parity,
+                     "wall_frac": value * 1e6 / world * bytes_per_flup / 1e9 / peak},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps,
                 "what": f"lbm_init from host geometry + {e2e_steps} steps + plane averages to host, all four solvers"},
@@ -768,16 +882,22 @@ def main():
                     help="even-step kernel: autotuned, or always the TMA-staged one")
     ap.add_argument("--bounce-back", action="store_true",
                     help="simple bounce-back on every wall link instead of CLI (Eq. (noslip), q = 1/2 forced)")
+    ap.add_argument("--wall-rule", choices=["auto", "paper", "safeguards"], default="auto",
+                    help="Eq. (CLI) wherever x_f2 exists (paper), or with the corner safeguards (q < 0.1 and "
+                         "two-cell gaps bounce back); auto: paper on the workloads where it was found stable")
+    ap.add_argument("--stability-steps", type=int, default=60000,
+                    help="cli-stability: steps per packing")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
     ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet", "glbm",
-                                           "homogenised", "grid-study", "re-sweep"],
+                                           "homogenised", "grid-study", "re-sweep", "cli-stability"],
                     default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
                          "warm versus cold start; unet: U-Net training steps; glbm: the homogenised model; "
                          "homogenised: the homogenised model against the pore-scale profile; grid-study, "
-                         "re-sweep: the resolution and Reynolds-number studies of the pore-scale profile")
+                         "re-sweep: the resolution and Reynolds-number studies of the pore-scale profile; "
+                         "cli-stability: growth of a perturbation of the rest state on every packing")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
@@ -805,6 +925,8 @@ def main():
         run_grid_study(args)
     elif args.workload == "re-sweep":
         run_re_sweep(args)
+    elif args.workload == "cli-stability":
+        run_cli_stability(args)
     elif args.converge:
         run_converge(args)
     else:

@@ -7,8 +7,8 @@
  * (equilibrium), (Macro), (collision), (streaming)) driven by a body force,
  * with central-linear-interpolation bounce-back on every wall link
  * (Sec. 2.2, Eq. (CLI); q = 1/2 is simple bounce-back, Eq. (noslip); links
- * without a second fluid node, across a two-cell gap or with q < 0.1 use
- * bounce-back), on
+ * without a second fluid node use bounce-back, and LBM_FLAG_CLI_SAFEGUARDS
+ * extends that to links across a two-cell gap or with q < 0.1), on
  * voxelised sphere packings (Sec. 3.1), with plane averages of the stream-wise
  * velocity (Sec. 3.1) and the Darcy permeability (Eq. (Darcy)).
  *
@@ -50,7 +50,9 @@ extern "C" {
 #define LBM_EPACKING (-4)     /* target porosity unreachable without overlap */
 #define LBM_ENAN (-5)         /* a NaN or Inf appeared in the velocity field */
 #define LBM_ENOTCONVERGED (-6)/* lbm_run_until reached max_steps */
-#define LBM_ETIMEOUT (-7)     /* a bounded device-side wait gave up */
+#define LBM_ETIMEOUT (-7)     /* a bounded device-side wait gave up; the solver
+                                 then refuses lbm_step/lbm_run_until (also
+                                 LBM_ETIMEOUT) until lbm_reset */
 #define LBM_ESIZE (-8)        /* workspace too small or misaligned */
 
 /* ---- storage precision of the populations ---- */
@@ -120,6 +122,16 @@ typedef struct {
  * fractions q are still computed and exported; every link reports the
  * bounce-back fallback. */
 #define LBM_FLAG_SIMPLE_BOUNCE_BACK 32
+/* Corner safeguards of Eq. (CLI).  By default (the paper's scheme) a wall
+ * link uses Eq. (CLI) whenever its second fluid node x_f2 = x_f1 - e_k exists
+ * and simple bounce-back only where x_f2 is solid.  With this flag two more
+ * kinds of link take simple bounce-back: links whose x_f1 - 2 e_k is solid
+ * (a two-cell gap, where the interpolations of the two walls feed each other)
+ * and links with q < 0.1 (a = (1-2q)/(1+2q) > 2/3).  In sharp corners of
+ * overlapping sphere packings (nodes with 10-14 of their 18 links cut) the
+ * paper's update was observed to grow without bound; the safeguards keep it
+ * bounded at the price of a half-way wall on those links. */
+#define LBM_FLAG_CLI_SAFEGUARDS 128
 
 /* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
  * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes
@@ -225,7 +237,8 @@ int lbm_schedule(const lbm_solver *solver, int32_t *grid_even, int32_t *grid_odd
                  int32_t *graph_steps);
 
 /* Re-initialise the populations of an existing solver (step count back to 0)
- * from dev_u0 (or rest when NULL). */
+ * from dev_u0 (or rest when NULL); clears the stale state that a timed-out
+ * step leaves (LBM_ETIMEOUT). */
 int lbm_reset(lbm_solver *solver, const float *dev_u0);
 
 /* Advance n >= 0 time steps (collision, Eq. (collision), then streaming,
@@ -306,10 +319,9 @@ int lbm_solver_info(const lbm_solver *solver, lbm_geometry_info *out);
  * link_cell/link_k/link_q/link_fallback[n_links]: one record per wall link in
  * (cell, k) order with the link fraction q of Eq. (CLI) and 1 when the link
  * uses simple bounce-back (a = 0) instead: when its second fluid node
- * x_f2 = x_f1 - e_k is solid, when x_f1 - 2 e_k is solid (a two-cell gap),
- * or when q < 0.1 (the wall within a tenth of a link of the node).  In the
- * sharp corners of overlapping sphere packings Eq. (CLI) on the last two
- * kinds of link was observed to grow without bound.
+ * x_f2 = x_f1 - e_k is solid, and with LBM_FLAG_CLI_SAFEGUARDS also when
+ * x_f1 - 2 e_k is solid (a two-cell gap) or when q < 0.1 (the wall within a
+ * tenth of a link of the node); every link with LBM_FLAG_SIMPLE_BOUNCE_BACK.
  * Synchronises the stream. */
 int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int32_t *link_cell,
                      int8_t *link_k, double *link_q, uint8_t *link_fallback);
@@ -317,9 +329,12 @@ int lbm_export_lists(lbm_solver *solver, int32_t *fluid_cell, int32_t *nbr, int3
 /* Self-test of failure detection: one warp on the solver's stream waits, with
  * the bounded mbarrier wait of the staged step kernels, on a barrier phase
  * that nothing completes; after max_polls polls (>= 1) it gives up and sets
- * the solver's status word.  Synchronises and returns what the synchronising
- * calls return after such an event: LBM_ETIMEOUT, with the word cleared and
- * the solver usable.  Touches no populations. */
+ * the solver's status word as a step kernel would.  Synchronises and returns
+ * what the synchronising calls return after such an event: LBM_ETIMEOUT,
+ * with the word cleared.  The solver then treats its state as stale, as after
+ * a real timeout (a block that gives up leaves its tile half-updated):
+ * lbm_step and lbm_run_until return LBM_ETIMEOUT until lbm_reset, while the
+ * read-only calls keep working.  Touches no populations itself. */
 int lbm_wait_selftest(lbm_solver *solver, int32_t max_polls);
 
 /* Shifted populations h_k = f_k - w_k of the current state (the streamed
@@ -338,9 +353,10 @@ int lbm_populations(lbm_solver *solver, float *dev_out);
  * lbm_plane_average.  The per-plane scratch is a fixed array of
  * LBM_STATIC_MAX_PLANES planes compiled into the library and kept on every GPU
  * that loads it until the process exits; nz > LBM_STATIC_MAX_PLANES is
- * rejected with LBM_EINVAL.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress), so make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
+ * rejected with LBM_EINVAL.  The first call in each device context (the
+ * current device's primary context; again after a cudaDeviceReset) looks up
+ * the array's device address with cudaGetSymbolAddress, so make that first
+ * call before any stream capture.  All calls share the array: calls that overlap on the GPU
  * (other streams or threads) race; each call overwrites every entry it uses.
  * No cudaMalloc, cudaFree or allocating library routine is called.
  * Synchronises `stream` (a cudaStream_t, NULL = default stream). */

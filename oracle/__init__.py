@@ -61,10 +61,10 @@ def _load():
         "orc_voxelize": (None, [_i, _i, _i, _i, _p, _i64, _p]),
         "orc_place_spheres": (_i, [_i, _i, _i, _i, _d, _d, _d, _d, _d, _i, _u64, _i64, _i64, _p, _p, _p]),
         "orc_link_q": (_d, [_i, _i, _i, _i, _d, _d, _p, _i64, _i, _i, _i, _i]),
-        "orc_build_lists": (_i, [_i, _i, _i, _i, _d, _d, _p, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _i]),
+        "orc_build_lists": (_i, [_i, _i, _i, _i, _d, _d, _p, _i64, _p, _p, _p, _p, _p, _p, _p, _p, _i, _i]),
         "orc_rates": (None, [_d, _d, _p, _p, _p]),
         "orc_equilibrium": (None, [_d, _p, _p]),
-        "orc_lbm_create": (_p, [_i, _i, _i, _i, _d, _d, _p, _i64, _d, _d, _d, _d, _d]),
+        "orc_lbm_create": (_p, [_i, _i, _i, _i, _d, _d, _p, _i64, _d, _d, _d, _d, _d, _i]),
         "orc_lbm_set_simple_bounce_back": (None, [_p]),
         "orc_lbm_destroy": (None, [_p]),
         "orc_lbm_init": (None, [_p, _p]),
@@ -159,14 +159,16 @@ def link_q(nx, ny, nz, periodic_z, xyzr, x, y, z, k, q_lo=0.5, q_hi=0.5) -> floa
                                     x, y, z, k))
 
 
-def build_lists(nx, ny, nz, periodic_z, xyzr, q_lo=0.5, q_hi=0.5, use_bins=False) -> dict:
+def build_lists(nx, ny, nz, periodic_z, xyzr, q_lo=0.5, q_hi=0.5, use_bins=False, safeguards=False) -> dict:
     """Fluid list, neighbour table and wall-link list (see lbm_oracle.c).
-    ``use_bins`` prunes the sphere search for large boxes (same result)."""
+    ``use_bins`` prunes the sphere search for large boxes (same result).
+    ``safeguards`` adds the two corner fallbacks (q < 0.1, two-cell gap) to the
+    paper's one (x_f2 solid)."""
     lib = _load()
     sp = np.ascontiguousarray(np.asarray(xyzr, np.float64).reshape(-1, 4))
     nf, nl = ctypes.c_int64(), ctypes.c_int64()
     rc = lib.orc_build_lists(nx, ny, nz, int(periodic_z), q_lo, q_hi, _ptr(sp), sp.shape[0],
-                             ctypes.byref(nf), ctypes.byref(nl), None, None, None, None, None, None, 0)
+                             ctypes.byref(nf), ctypes.byref(nl), None, None, None, None, None, None, 0, 0)
     assert rc == 0
     fluid = np.zeros(nf.value, np.int32)
     nbr = np.zeros((18, nf.value), np.int32)
@@ -176,7 +178,7 @@ def build_lists(nx, ny, nz, periodic_z, xyzr, q_lo=0.5, q_hi=0.5, use_bins=False
     lf = np.zeros(nl.value, np.uint8)
     rc = lib.orc_build_lists(nx, ny, nz, int(periodic_z), q_lo, q_hi, _ptr(sp), sp.shape[0],
                              ctypes.byref(nf), ctypes.byref(nl), _ptr(fluid), _ptr(nbr), _ptr(lc),
-                             _ptr(lk), _ptr(lq), _ptr(lf), int(use_bins))
+                             _ptr(lk), _ptr(lq), _ptr(lf), int(use_bins), int(safeguards))
     assert rc == 0
     return {"fluid_cell": fluid, "nbr": nbr, "link_cell": lc, "link_k": lk, "link_q": lq,
             "link_fallback": lf}
@@ -194,17 +196,21 @@ def set_threads(n: int) -> None:
 # The LBM
 # --------------------------------------------------------------------------
 class Lattice:
-    """Dense two-array FP64 TRT/CLI lattice; fields are [.., nz, ny, nx]."""
+    """Dense two-array FP64 TRT/CLI lattice; fields are [.., nz, ny, nx].
+
+    Eq. (CLI) on every wall link with a second fluid node (the paper's scheme);
+    ``cli_safeguards`` also turns links with q < 0.1 or across a two-cell gap
+    into simple bounce-back, ``simple_bounce_back`` every link."""
 
     def __init__(self, nx, ny, nz, periodic_z, xyzr=(), tau=0.8, lam=3.0 / 16.0, g=(1e-6, 0.0, 0.0),
-                 q_lo=0.5, q_hi=0.5, simple_bounce_back=False):
+                 q_lo=0.5, q_hi=0.5, simple_bounce_back=False, cli_safeguards=False):
         self._lib = _load()
         sp = np.ascontiguousarray(np.asarray(xyzr, np.float64).reshape(-1, 4))
         self.shape = (nz, ny, nx)
         self.ncell = nx * ny * nz
         self.g = tuple(float(v) for v in g)
         self._h = self._lib.orc_lbm_create(nx, ny, nz, int(periodic_z), q_lo, q_hi, _ptr(sp),
-                                           sp.shape[0], tau, lam, *self.g)
+                                           sp.shape[0], tau, lam, *self.g, int(cli_safeguards))
         if not self._h:
             raise MemoryError("oracle lattice allocation failed")
         if simple_bounce_back:

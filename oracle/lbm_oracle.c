@@ -30,9 +30,10 @@
  * F_k = 3 w_k e_k.g added after relaxation with the equilibrium built from the
  * pre-collision momentum j, and the reported velocity u = j + g/2; full
  * (unshifted) populations with rho = sum f; the second fluid node of a link is
- * x_f2 = x_f1 - e_k, and the link falls back to bounce-back when x_f2 is solid,
- * when x_f1 - 2 e_k is solid, or when q < 0.1 (stability safeguards for sharp
- * corners, see orc_link_fallback);
+ * x_f2 = x_f1 - e_k, and the link falls back to bounce-back when x_f2 is solid
+ * (Eq. (CLI) has no second node there); optionally (the "safeguards", off by
+ * default) also when x_f1 - 2 e_k is solid or when q < 0.1, which stabilises
+ * sharp corners of overlapping packings (see orc_link_fallback);
  * q is the first point of the link on a solid surface (smallest entry
  * parameter);
  * seeded sphere placement (SplitMix64) stands in for the rigid-body packing.
@@ -431,9 +432,10 @@ static int64_t orc_neighbour(const orc_box *b, int x, int y, int z, int k)
 
 /* Bounce-back fallback of link (x, k) with fraction q.  Eq. (CLI) needs the
  * second fluid node x_f2 = x_f1 - e_k, so the link uses simple bounce-back
- * (a = 0) when x_f2 is solid.  Two more cases take bounce-back because the
- * FP64 update was observed to grow without bound there, in the sharp corners
- * of overlapping sphere packings (nodes with most of their 18 links cut):
+ * (a = 0) when x_f2 is solid: this is the only fallback of the paper's scheme.
+ * With `safeguards` set, two more cases take bounce-back because the FP64
+ * update was observed to grow without bound there, in the sharp corners of
+ * overlapping sphere packings (nodes with most of their 18 links cut):
  *   - x_f2 is itself a wall node on the link's line (x_f1 - 2 e_k solid: a
  *     two-cell gap, where the two interpolations feed each other);
  *   - q < ORC_CLI_QMIN: the wall within a tenth of a link of the node, where
@@ -441,11 +443,14 @@ static int64_t orc_neighbour(const orc_box *b, int x, int y, int z, int k)
  * Either case alone left some corners unstable; together they stabilised
  * every one found. */
 #define ORC_CLI_QMIN 0.1
-static int orc_link_fallback(const orc_box *b, const uint8_t *solid, int x, int y, int z, int k, double q)
+static int orc_link_fallback(const orc_box *b, const uint8_t *solid, int x, int y, int z, int k, double q,
+                             int safeguards)
 {
     const int kb = orc_opp(k);
     int64_t c2 = orc_neighbour(b, x, y, z, kb);
-    if (c2 < 0 || solid[c2] || q < ORC_CLI_QMIN) return 1;
+    if (c2 < 0 || solid[c2]) return 1;
+    if (!safeguards) return 0;
+    if (q < ORC_CLI_QMIN) return 1;
     int x2 = orc_wrap(x + ORC_EX[kb], b->nx), y2 = orc_wrap(y + ORC_EY[kb], b->ny), z2 = z + ORC_EZ[kb];
     if (b->periodic_z) z2 = orc_wrap(z2, b->nz);
     int64_t c3 = orc_neighbour(b, x2, y2, z2, kb);
@@ -459,13 +464,14 @@ static int orc_link_fallback(const orc_box *b, const uint8_t *solid, int x, int 
 /* nbr[(k-1)*nf+i]: fluid index of the neighbour along e_k, -1 when solid.    */
 /* links          : one record per (fluid cell, k) with a solid neighbour,   */
 /*                  sorted by (cell, k): cell index i, k, q, and whether the  */
-/*                  link falls back to bounce-back (orc_link_fallback).       */
+/*                  link falls back to bounce-back (orc_link_fallback, with   */
+/*                  the corner safeguards when `safeguards` is set).          */
 /* Call with fluid_cell == NULL to get counts only.                           */
 /* ------------------------------------------------------------------------- */
 int orc_build_lists(int nx, int ny, int nz, int periodic_z, double q_lo, double q_hi,
                     const double *xyzr, int64_t n, int64_t *nf_out, int64_t *nlinks_out,
                     int32_t *fluid_cell, int32_t *nbr, int32_t *link_cell, int8_t *link_k,
-                    double *link_q, uint8_t *link_fallback, int use_bins)
+                    double *link_q, uint8_t *link_fallback, int use_bins, int safeguards)
 {
     orc_box b = {nx, ny, nz, periodic_z, q_lo, q_hi};
     int64_t ncell = (int64_t)nx * ny * nz;
@@ -496,7 +502,7 @@ int orc_build_lists(int nx, int ny, int nz, int periodic_z, double q_lo, double 
                         link_k[nl] = (int8_t)k;
                         link_q[nl] = use_bins ? orc_link_q_binned(&b, xyzr, &bins, x, y, z, k)
                                               : orc_link_q_impl(&b, xyzr, n, x, y, z, k);
-                        link_fallback[nl] = (uint8_t)orc_link_fallback(&b, solid, x, y, z, k, link_q[nl]);
+                        link_fallback[nl] = (uint8_t)orc_link_fallback(&b, solid, x, y, z, k, link_q[nl], safeguards);
                     }
                     ++nl;
                 }
@@ -553,7 +559,7 @@ void orc_rates(double tau, double lambda, double *omega_p, double *omega_m, doub
 
 orc_lbm *orc_lbm_create(int nx, int ny, int nz, int periodic_z, double q_lo, double q_hi,
                         const double *xyzr, int64_t n, double tau, double lambda, double gx,
-                        double gy, double gz)
+                        double gy, double gz, int safeguards)
 {
     orc_lbm *s = (orc_lbm *)calloc(1, sizeof(orc_lbm));
     if (!s) return NULL;
@@ -596,7 +602,7 @@ orc_lbm *orc_lbm_create(int nx, int ny, int nz, int periodic_z, double q_lo, dou
                     if (cn >= 0 && !s->solid[cn]) continue;
                     double q = orc_link_q_binned(&s->b, xyzr, &bins, x, y, z, k);
                     s->link_k[l] = (int8_t)k;
-                    s->link_a[l] = orc_link_fallback(&s->b, s->solid, x, y, z, k, q) ? 0.0
+                    s->link_a[l] = orc_link_fallback(&s->b, s->solid, x, y, z, k, q, safeguards) ? 0.0
                                                                                   : (1.0 - 2.0 * q) / (1.0 + 2.0 * q);
                     ++l;
                 }

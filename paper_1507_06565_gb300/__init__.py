@@ -36,6 +36,7 @@ LBM_FLAG_NO_GRAPH = 4
 LBM_FLAG_NO_AUTOTUNE = 8
 LBM_FLAG_SIMPLE_BOUNCE_BACK = 32
 LBM_FLAG_STAGED_EVEN = 64
+LBM_FLAG_CLI_SAFEGUARDS = 128
 
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1
@@ -384,6 +385,14 @@ class Solver:
         _check(load_library().lbm_export_lists(self._h, *[_np_ptr(out[k]) for k in
                                                            ("fluid_cell", "nbr", "link_cell", "link_k", "link_q",
                                                             "link_fallback")]), "lbm_export_lists")
+        return out
+
+    def link_fallback(self) -> np.ndarray:
+        """Per wall link (in (cell, k) order): 1 where it takes simple
+        bounce-back instead of Eq. (CLI)."""
+        out = np.zeros(self.info()["n_links"], np.uint8)
+        _check(load_library().lbm_export_lists(self._h, None, None, None, None, None, _np_ptr(out)),
+               "lbm_export_lists")
         return out
 
     def populations(self):

@@ -105,7 +105,7 @@ static bool params_ok(const lbm_params *p)
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return false;
     const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE |
-                          LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_STAGED_EVEN;
+                          LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_STAGED_EVEN | LBM_FLAG_CLI_SAFEGUARDS;
     if ((p->flags & ~known) != 0) return false;
     if ((p->flags & LBM_FLAG_NEIGHBOUR_TABLE) && (p->flags & LBM_FLAG_ROW_NEIGHBOURS)) return false;
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
@@ -376,7 +376,9 @@ int lbm_batch_part_info(const lbm_solver *s, int32_t part, lbm_geometry_info *in
 
 // Synchronise the solver's stream and read the step kernels' status word:
 // LBM_ETIMEOUT (and the word cleared) if a bounded device-side wait gave up
-// since the last check.
+// since the last check.  The state is then marked stale: a block that gave
+// up returned without finishing its tile, so lbm_step refuses to continue
+// until lbm_reset.
 static int sync_checked(lbm_solver *s)
 {
     int st = 0;
@@ -384,6 +386,7 @@ static int sync_checked(lbm_solver *s)
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return LBM_ECUDA;
     if (st) {
+        s->stale = true;
         if (cudaMemsetAsync(s->status, 0, sizeof(int), s->stream) != cudaSuccess) return LBM_ECUDA;
         return LBM_ETIMEOUT;
     }
@@ -409,6 +412,7 @@ int lbm_batch_permeability(lbm_solver *s, double *k_out)
 int lbm_reset(lbm_solver *s, const float *dev_u0)
 {
     if (!s) return LBM_EINVAL;
+    s->stale = false;
     s->has_prev = false;
     for (Part &P : s->parts) P.has_prev_profile = false;
     return launch_init(*s, dev_u0);
@@ -417,6 +421,7 @@ int lbm_reset(lbm_solver *s, const float *dev_u0)
 int lbm_step(lbm_solver *s, int64_t n)
 {
     if (!s || n < 0) return LBM_EINVAL;
+    if (s->stale) return LBM_ETIMEOUT;
     return launch_steps(*s, n);
 }
 
@@ -572,6 +577,7 @@ int lbm_run_until(lbm_solver *s, double tol, int64_t interval, int64_t max_steps
 {
     if (!s || interval < 1 || max_steps < 0 || !(tol > 0.0)) return LBM_EINVAL;
     if (criterion != LBM_CONVERGE_FIELD && criterion != LBM_CONVERGE_PROFILE) return LBM_EINVAL;
+    if (s->stale) return LBM_ETIMEOUT;
     auto residual = [&](double *r) {
         return criterion == LBM_CONVERGE_FIELD ? lbm_residual(s, r) : lbm_profile_residual(s, r);
     };
@@ -632,7 +638,8 @@ int lbm_export_lists(lbm_solver *s, int32_t *fluid_cell, int32_t *nbr, int32_t *
         return LBM_ECUDA;
     if (link_cell || link_k || link_fallback) {
         // links in (cell, k) order from the link masks; a link falls back to
-        // bounce-back when x - e_k or x - 2 e_k is solid or q < kCliQmin
+        // bounce-back when x - e_k is solid, and with the corner safeguards
+        // also when x - 2 e_k is solid or q < kCliQmin
         std::vector<uint32_t> mask(nf ? nf : 1);
         std::vector<double> qs;
         std::vector<int32_t> nb;
@@ -657,9 +664,10 @@ int lbm_export_lists(lbm_solver *s, int32_t *fluid_cell, int32_t *nbr, int32_t *
                     if (link_cell) link_cell[l] = (int32_t)i;
                     if (link_k) link_k[l] = (int8_t)k;
                     if (link_fallback) {
+                        const bool guard = (s->params.flags & LBM_FLAG_CLI_SAFEGUARDS) != 0;
                         bool fb = (s->params.flags & LBM_FLAG_SIMPLE_BOUNCE_BACK) || ((mask[i] >> opp(k)) & 1u) ||
-                                  qs[l] < kCliQmin;
-                        if (!fb) fb = (mask[nb[(size_t)(opp(k) - 1) * nf + i]] >> opp(k)) & 1u;
+                                  (guard && qs[l] < kCliQmin);
+                        if (!fb && guard) fb = (mask[nb[(size_t)(opp(k) - 1) * nf + i]] >> opp(k)) & 1u;
                         link_fallback[l] = (uint8_t)fb;
                     }
                     ++l;

@@ -12,8 +12,8 @@
 // then over the whole solver: link counts per aligned group of 32 fluid cells
 // and their exclusive scan; and again per part:
 //   5. link fraction q and CLI coefficient a = (1-2q)/(1+2q) per link
-//      (a = 0, bounce-back, when the second node x - e_k is solid, when
-//      x - 2 e_k is solid, or when q < 0.1).
+//      (a = 0, bounce-back, when the second node x - e_k is solid; with the
+//      corner safeguards also when x - 2 e_k is solid or when q < 0.1).
 // The index map and the mask live in the population region, which is written
 // only afterwards by the initialisation.
 #include <cstdio>
@@ -200,6 +200,7 @@ struct LinkArgs {
     int nbx, nby;
     double q_lo, q_hi;
     int simple_bounce_back;   // every link a = 0 (LBM_FLAG_SIMPLE_BOUNCE_BACK)
+    int safeguards;           // LBM_FLAG_CLI_SAFEGUARDS
 };
 
 // 5. link fractions and CLI coefficients of the cells of one part.  The grid
@@ -267,12 +268,13 @@ __global__ void k_links(LinkArgs a)
             const double s = sphere_entry((double)x - im.x, (double)y - im.y, (double)z - im.z, kx, ky, kz, im.r);
             if (s < q) q = s;
         }
-        // bounce-back when the second node x_f2 = x - e_k is solid, is itself a
-        // wall node on the link's line (x - 2 e_k solid), or when the wall is
-        // within kCliQmin of the node: Eq. (CLI) grows without bound in such
+        // bounce-back when the second node x_f2 = x - e_k is solid (Eq. (CLI)
+        // has no second node); with the safeguards also when x_f2 is itself a
+        // wall node on the link's line (x - 2 e_k solid) or when the wall is
+        // within kCliQmin of the node: Eq. (CLI) can grow without bound in such
         // sharp corners of overlapping packings
-        bool fallback = a.simple_bounce_back || ((mj >> opp(k)) & 1u) || q < kCliQmin;
-        if (!fallback) {
+        bool fallback = a.simple_bounce_back || ((mj >> opp(k)) & 1u) || (a.safeguards && q < kCliQmin);
+        if (!fallback && a.safeguards) {
             const int32_t x2 = a.nbr[(size_t)(opp(k) - 1) * a.n_pad + c_i];
             fallback = (a.lmask[x2] >> opp(k)) & 1u;
         }
@@ -396,7 +398,8 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
         const int32_t begin = P.fluid_off, end = P.fluid_off + P.n_fluid;
         LinkArgs la{s.fluid_cell, s.nbr, s.lmask, s.warp_off, d_bstart, d_img, s.link_a, s.link_q, begin, end,
                     s.n_fluid, s.n_pad, P.cell_base, P.box.nx, P.box.ny, P.box.nz, P.box.periodic_z, bins.nbx,
-                    bins.nby, P.box.q_lo, P.box.q_hi, (s.params.flags & LBM_FLAG_SIMPLE_BOUNCE_BACK) ? 1 : 0};
+                    bins.nby, P.box.q_lo, P.box.q_hi, (s.params.flags & LBM_FLAG_SIMPLE_BOUNCE_BACK) ? 1 : 0,
+                    (s.params.flags & LBM_FLAG_CLI_SAFEGUARDS) ? 1 : 0};
         k_links<<<blocks_for(end - (begin & ~31)), kBlock, 0, st>>>(la);
         LBM_CUDA_TRY(cudaGetLastError());
         // the host bins must outlive their (pageable, staged) copies: synchronise

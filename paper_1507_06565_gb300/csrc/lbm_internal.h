@@ -35,9 +35,10 @@ namespace lbm {
 constexpr int kQ = 19;
 constexpr int kBlock = 256;   // threads per block of the per-cell kernels
 constexpr int kBinEdge = 8;   // edge (cells) of the sphere-image bins
-// Links whose wall lies closer than this fraction of the link to the node use
-// simple bounce-back instead of Eq. (CLI) (stability in sharp corners, with
-// the two-cell-gap rule of k_links).
+// With LBM_FLAG_CLI_SAFEGUARDS, links whose wall lies closer than this
+// fraction of the link to the node use simple bounce-back instead of
+// Eq. (CLI) (stability in sharp corners, with the two-cell-gap rule of
+// k_links).
 constexpr double kCliQmin = 0.1;
 
 // ---------------------------------------------------------------------------
@@ -187,6 +188,10 @@ struct Solver {
     float *part_shift = nullptr;
     int32_t *part_foff = nullptr;
     int *status = nullptr;   // set by a step kernel whose bounded wait gave up
+    // a step kernel gave up a wait (reported once as LBM_ETIMEOUT): its block
+    // left the tile's populations half-updated, so steps are refused until
+    // lbm_reset re-initialises the state
+    bool stale = false;
     ~Solver();
 };
 

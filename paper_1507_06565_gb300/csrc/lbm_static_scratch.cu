@@ -11,8 +11,14 @@
 //
 // The scratch lives in device global memory of every GPU that loads the
 // library, for as long as the library stays loaded.  Host code cannot use the
-// array's name as a device address, so its address is looked up once per
-// device with cudaGetSymbolAddress (on the first call made on that device).
+// array's name as a device address, so its address is looked up with
+// cudaGetSymbolAddress on the first call made in each device context (the
+// primary context of the current device, as the runtime uses it).  The cache
+// is keyed on the context's unique id: after a cudaDeviceReset the module is
+// loaded again into a new context, where the array may sit elsewhere, and the
+// next call looks it up afresh.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -29,7 +35,11 @@ __device__ __align__(256) static double g_plane_scratch[3 * LBM_STATIC_MAX_PLANE
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;   // 0: never looked up
+    double *ptr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 
 __device__ double static_block_sum(double v)
 {
@@ -68,18 +78,51 @@ __global__ void __launch_bounds__(kStaticThreads) k_plane_average_dense(const fl
     }
 }
 
-// Device address of the scratch on the current device, looked up once.
+// Unique id of the current CUDA context (0 when none is current or the driver
+// does not provide the query).  The driver functions are reached through the
+// runtime's entry-point lookup, so the library needs no link to libcuda.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (GetCurrent)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (GetId)f;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch in the current device context: looked up on
+// the first call in that context and kept for the next ones.
 int scratch_for_current_device(double **ptr)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ECUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot &slot = g_scratch[dev];
+    const unsigned long long id = current_context_id();
+    if (id == 0 || slot.ctx_id != id || !slot.ptr) {
+        // the lookup also makes the device's primary context current
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_plane_scratch) != cudaSuccess || !p) return LBM_ECUDA;
-        g_scratch_ptr[dev] = (double *)p;
+        slot.ptr = (double *)p;
+        slot.ctx_id = current_context_id();
     }
-    *ptr = g_scratch_ptr[dev];
+    *ptr = slot.ptr;
     return LBM_OK;
 }
 

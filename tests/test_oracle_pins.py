@@ -86,8 +86,9 @@ def test_splitmix64_published_outputs():
 # for the velocity u = j + g/2.  With q = 1/2 (Eq. (noslip)) and
 # Lambda = 3/16 it vanishes: the exact half-way wall quoted in Sec. 2.1.
 # ---------------------------------------------------------------------------
-def _channel(nz, tau, lam, q_lo, q_hi, g=1e-6, simple_bounce_back=False):
-    lat = O.Lattice(2, 2, nz, False, (), tau, lam, (g, 0.0, 0.0), q_lo, q_hi, simple_bounce_back).init()
+def _channel(nz, tau, lam, q_lo, q_hi, g=1e-6, simple_bounce_back=False, cli_safeguards=False):
+    lat = O.Lattice(2, 2, nz, False, (), tau, lam, (g, 0.0, 0.0), q_lo, q_hi, simple_bounce_back,
+                    cli_safeguards).init()
     H = nz - 2
     lat.step(int(40 * H * H / (math.pi ** 2 * lat.nu)) + 200)
     _, u = lat.moments()
@@ -115,7 +116,8 @@ def test_poiseuille_half_way_exact(tau):
     (0.8, 3 / 16, 0.3, 0.8),   # CLI off-grid walls
     (1.4, 3 / 16, 0.3, 0.8),   # same walls, other viscosity: same q-dependence
     (1.4, 0.25, 0.15, 1.0),    # CLI at q = 1 and small q
-    (0.7, 0.1, 0.1, 0.65),     # smallest q that keeps Eq. (CLI)
+    (0.7, 0.1, 0.1, 0.65),     # smallest q that keeps Eq. (CLI) under the safeguards
+    (0.7, 0.1, 0.05, 0.65),    # the paper's Eq. (CLI) below it
 ])
 def test_channel_wall_slip_closed_form(tau, lam, q_lo, q_hi):
     lat, ux, exact, _ = _channel(18, tau, lam, q_lo, q_hi)
@@ -144,11 +146,15 @@ def test_simple_bounce_back_places_walls_half_way():
 
 
 def test_channel_small_q_wall_is_bounce_back():
-    """A wall closer than 0.1 of a link to the node takes simple bounce-back:
-    the same profile as a wall at q = 1/2."""
-    _, ux, _, _ = _channel(18, 0.7, 0.1, 0.05, 0.65)
+    """With the corner safeguards, a wall closer than 0.1 of a link to the node
+    takes simple bounce-back: the same profile as a wall at q = 1/2; without
+    them (the paper's scheme) the same wall follows Eq. (CLI) and the profile
+    moves by a measurable amount."""
+    _, ux, _, _ = _channel(18, 0.7, 0.1, 0.05, 0.65, cli_safeguards=True)
     _, _, exact, _ = _channel(18, 0.7, 0.1, 0.5, 0.65)
     assert np.max(np.abs(ux - exact)) <= 1e-9 * np.max(exact)
+    _, ux_paper, _, _ = _channel(18, 0.7, 0.1, 0.05, 0.65)
+    assert np.max(np.abs(ux_paper - exact)) > 1e-2 * np.max(exact)
 
 
 def test_cli_second_order_in_resolution():
@@ -256,8 +262,8 @@ CORNERS = {
 }
 
 
-def _growth(nx, ny, nz, periodic_z, spheres, first, then):
-    lat = O.Lattice(nx, ny, nz, periodic_z, spheres, 0.8, 3 / 16, (0.0, 0.0, 0.0))
+def _growth(nx, ny, nz, periodic_z, spheres, first, then, cli_safeguards=False):
+    lat = O.Lattice(nx, ny, nz, periodic_z, spheres, 0.8, 3 / 16, (0.0, 0.0, 0.0), cli_safeguards=cli_safeguards)
     rng = np.random.default_rng(0)
     lat.init(1e-6 * rng.standard_normal((3, nz, ny, nx)))
     lat.step(first)
@@ -271,12 +277,21 @@ def _growth(nx, ny, nz, periodic_z, spheres, first, then):
 @pytest.mark.parametrize("corner", sorted(CORNERS))
 def test_sharp_corners_are_stable(corner):
     """Cuts of seeded overlapping packings around sharp corners (nodes with
-    10-14 of their 18 links cut, several at q < 0.1): with the bounce-back
-    fallback on links across two-cell gaps and links with q < 0.1, a
-    perturbation of the rest state does not grow."""
+    10-14 of their 18 links cut, several at q < 0.1): with the corner
+    safeguards (bounce-back on links across two-cell gaps and links with
+    q < 0.1), a perturbation of the rest state does not grow."""
     nx, ny, nz, pz, sp = CORNERS[corner]()
-    g = _growth(nx, ny, nz, pz, sp, 2000, 14000)
+    g = _growth(nx, ny, nz, pz, sp, 2000, 14000, cli_safeguards=True)
     assert np.isfinite(g) and g <= 1.001
+
+
+def test_paper_cli_grows_in_a_sharp_corner():
+    """Why the safeguards exist: the paper's Eq. (CLI) on every link with a
+    second fluid node lets the same perturbation grow in the corner of REV
+    cube 17 (x17 over 14000 steps)."""
+    nx, ny, nz, pz, sp = CORNERS["cube 151 seed 4017"]()
+    g = _growth(nx, ny, nz, pz, sp, 2000, 14000)
+    assert not g <= 2.0
 
 
 def test_rest_state_is_invariant_with_cli_walls():
@@ -401,11 +416,12 @@ def test_link_q_against_bisection():
         assert abs(qb - lists["link_q"][li]) < 1e-12
 
 
-def test_lists_are_consistent():
+@pytest.mark.parametrize("safeguards", [False, True], ids=["paper-cli", "safeguards"])
+def test_lists_are_consistent(safeguards):
     nx, ny, nz = 16, 12, 14
     sp, _, rc = O.place_spheres(nx, ny, nz, False, 1.0, 7.0, 2.0, 3.0, 0.7, False, 5)
     assert rc == 0
-    L = O.build_lists(nx, ny, nz, False, sp, q_lo=0.25, q_hi=0.5)
+    L = O.build_lists(nx, ny, nz, False, sp, q_lo=0.25, q_hi=0.5, safeguards=safeguards)
     mask = O.voxelize(nx, ny, nz, False, sp).reshape(-1)
     fluid = L["fluid_cell"]
     assert (fluid == np.flatnonzero(mask == 0)).all()
@@ -427,11 +443,14 @@ def test_lists_are_consistent():
     want = [(i, k) for i in range(nf) for k in range(1, 19) if nbr[k - 1][i] < 0]
     assert list(zip(lc.tolist(), lk.tolist())) == want
     assert ((L["link_q"] > 0) & (L["link_q"] <= 1)).all()
-    # bounce-back fallback: x - e_k solid, x - 2 e_k solid (two-cell gap), or
-    # the wall within 0.1 of the node
+    # bounce-back fallback: x - e_k solid (Eq. (CLI) has no second node); with
+    # the safeguards also x - 2 e_k solid (two-cell gap) or the wall within
+    # 0.1 of the node
     def fallback(i, k, q):
         j = nbr[O.opposite(k) - 1][i]
-        return j < 0 or nbr[O.opposite(k) - 1][j] < 0 or q < 0.1
+        if j < 0:
+            return True
+        return safeguards and (nbr[O.opposite(k) - 1][j] < 0 or q < 0.1)
     fb = np.array([fallback(i, k, q) for (i, k), q in zip(want, L["link_q"])])
     assert (L["link_fallback"].astype(bool) == fb).all()
     assert fb.any() and not fb.all()
