@@ -293,8 +293,16 @@ int lbm_mass(lbm_solver *solver, double *mean_drho);
  * Eq. (CLI), a w - a w + w = w, all commute with it), so velocities are
  * unchanged in exact arithmetic; it keeps the stored populations small so
  * that reduced-precision storage keeps its resolution in long runs.
- * *shift_out (may be NULL) receives the scheduled shift.  Synchronises the
- * stream. */
+ * In the same way it refreshes the reference populations of the solver's
+ * translation-invariant planes (fully fluid planes whose neighbour planes are
+ * fully fluid too, e.g. the free channel above a porous layer): there every
+ * slot stores its population minus the equilibrium f^eq(1, u_z) of the
+ * plane's mean velocity, so that storage rounding acts on the small
+ * non-equilibrium part only (rounding that is the same at every cell of such
+ * a plane would otherwise act like a spurious body force).  The next step
+ * switches to the new references; the stored values change, the populations
+ * they represent do not.  *shift_out (may be NULL) receives the scheduled
+ * shift.  Synchronises the stream. */
 int lbm_recenter(lbm_solver *solver, double *shift_out);
 
 #define LBM_CONVERGE_FIELD 0    /* lbm_residual */
@@ -306,6 +314,28 @@ int lbm_recenter(lbm_solver *solver, double *shift_out);
  * residual.  LBM_ENOTCONVERGED after max_steps, LBM_ENAN on divergence. */
 int lbm_run_until(lbm_solver *solver, double tol, int64_t interval, int64_t max_steps, int32_t criterion,
                   int64_t *steps_done, double *res_out);
+
+/* Checkpoint and resume (the paper has no counterpart; long runs to steady
+ * state at 10^5-10^6 steps need it).  A checkpoint is a host byte buffer of
+ * lbm_checkpoint_size() bytes holding the stored populations at the current
+ * parity, the step count, the pending density shift, the reference
+ * populations and the residual histories; not the lists, which follow from
+ * the geometry.  lbm_save copies the state into host_buf (LBM_ESIZE if bytes
+ * is too small; LBM_ETIMEOUT for a stale solver).  lbm_load restores it into
+ * a solver created from the same geometry and the same tau, lambda, g,
+ * storage and wall rule (else LBM_EINVAL); the steps after it give the same
+ * bits as the uninterrupted run would.  Both synchronise the stream; the
+ * buffer is caller-owned and may be written to a file as it is (host byte
+ * order). */
+int lbm_checkpoint_size(const lbm_solver *solver, size_t *bytes);
+int lbm_save(lbm_solver *solver, void *host_buf, size_t bytes);
+int lbm_load(lbm_solver *solver, const void *host_buf, size_t bytes);
+
+/* Number of planes (over all parts) whose slots store populations relative
+ * to the plane's reference equilibrium (see lbm_recenter): fully fluid planes
+ * whose neighbour planes are fully fluid and lie in tiles of 256 cells that
+ * hold only such planes' cells. */
+int lbm_reference_planes(const lbm_solver *solver, int32_t *n_planes);
 
 /* Steps taken since lbm_init/lbm_reset. */
 int lbm_steps_done(const lbm_solver *solver, int64_t *steps);

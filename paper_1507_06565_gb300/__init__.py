@@ -109,6 +109,10 @@ SIGNATURES = {
     "lbm_recenter": (_I, [_P, ctypes.POINTER(_D)]),
     "lbm_run_until": (_I, [_P, _D, _I64, _I64, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D)]),
     "lbm_steps_done": (_I, [_P, ctypes.POINTER(_I64)]),
+    "lbm_reference_planes": (_I, [_P, ctypes.POINTER(_I32)]),
+    "lbm_checkpoint_size": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "lbm_save": (_I, [_P, _P, _SZ]),
+    "lbm_load": (_I, [_P, _P, _SZ]),
     "lbm_solver_info": (_I, [_P, ctypes.POINTER(lbm_geometry_info)]),
     "lbm_export_lists": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "lbm_populations": (_I, [_P, _P]),
@@ -386,6 +390,27 @@ class Solver:
                                                            ("fluid_cell", "nbr", "link_cell", "link_k", "link_q",
                                                             "link_fallback")]), "lbm_export_lists")
         return out
+
+    def save(self) -> bytes:
+        """Checkpoint of the solver's state (lbm_save) as bytes."""
+        n = _SZ()
+        lib = load_library()
+        _check(lib.lbm_checkpoint_size(self._h, ctypes.byref(n)), "lbm_checkpoint_size")
+        buf = np.zeros(int(n.value), np.uint8)
+        _check(lib.lbm_save(self._h, _np_ptr(buf), buf.size), "lbm_save")
+        return buf.tobytes()
+
+    def load(self, data: bytes) -> None:
+        """Resume from a checkpoint of the same problem (lbm_load)."""
+        buf = np.frombuffer(data, np.uint8).copy()
+        _check(load_library().lbm_load(self._h, _np_ptr(buf), buf.size), "lbm_load")
+
+    def reference_planes(self) -> int:
+        """Planes whose slots store populations relative to the plane's
+        reference equilibrium (refreshed by recenter())."""
+        n = _I32()
+        _check(load_library().lbm_reference_planes(self._h, ctypes.byref(n)), "lbm_reference_planes")
+        return n.value
 
     def link_fallback(self) -> np.ndarray:
         """Per wall link (in (cell, k) order): 1 where it takes simple

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["lbm_geometry.cpp", "lbm_api.cpp", "lbm_build.cu", "lbm_step.cu", "lbm_post.cu", "lbm_static_scratch.cu",
+SOURCES = ["lbm_geometry.cpp", "lbm_api.cpp", "lbm_checkpoint.cpp", "lbm_build.cu", "lbm_step.cu", "lbm_post.cu", "lbm_static_scratch.cu",
            "lbm_sdf.cu", "unet.cu", "glbm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

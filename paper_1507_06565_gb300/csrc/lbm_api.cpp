@@ -67,6 +67,10 @@ Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size
     L.part_shift = take((size_t)L.n_parts * 4);
     L.part_foff = take((size_t)(L.n_parts + 1) * 4);
     L.status = take(sizeof(int));
+    L.ref = take((size_t)n_planes * kRefStride * 4);
+    L.ref_next = take((size_t)n_planes * kRefStride * 4);
+    L.tile_ref = take((size_t)n_pad / kBlock * 8);
+    L.plane_flag = take((size_t)n_planes);
     L.total = off;
     return L;
 }
@@ -211,6 +215,10 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->part_shift = (float *)(s->ws + L.part_shift);
     s->part_foff = (int32_t *)(s->ws + L.part_foff);
     s->status = (int *)(s->ws + L.status);
+    s->ref = (float *)(s->ws + L.ref);
+    s->ref_next = (float *)(s->ws + L.ref_next);
+    s->tile_ref = (int2 *)(s->ws + L.tile_ref);
+    s->plane_flag = (uint8_t *)(s->ws + L.plane_flag);
     const bool single = geoms.size() == 1;
     s->n_words = (s->box.nx + 31) / 32;
     s->x_bits = x_bits_for(s->box.nx);
@@ -568,6 +576,10 @@ int lbm_recenter(lbm_solver *s, double *shift_out)
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return LBM_ECUDA;
     s->shift_pending = true;
+    // new reference populations from the same velocity field (part_masses
+    // ran the moments kernel); the next step switches to them
+    rc = launch_reference_update(*s);
+    if (rc != LBM_OK) return rc;
     if (shift_out) *shift_out = all;
     return LBM_OK;
 }
@@ -600,6 +612,15 @@ int lbm_run_until(lbm_solver *s, double tol, int64_t interval, int64_t max_steps
     if (steps_done) *steps_done = done;
     if (res_out) *res_out = res;
     return rc;
+}
+
+int lbm_reference_planes(const lbm_solver *s, int32_t *n_planes)
+{
+    if (!s || !n_planes) return LBM_EINVAL;
+    int32_t n = 0;
+    for (uint8_t f : s->plane_referenced) n += f ? 1 : 0;
+    *n_planes = n;
+    return LBM_OK;
 }
 
 int lbm_steps_done(const lbm_solver *s, int64_t *steps)

@@ -16,6 +16,7 @@
 //      corner safeguards also when x - 2 e_k is solid or when q < 0.1).
 // The index map and the mask live in the population region, which is written
 // only afterwards by the initialisation.
+#include <algorithm>
 #include <cstdio>
 
 #include "lbm_internal.h"
@@ -320,6 +321,49 @@ __global__ void k_dense_tiles(const int32_t *__restrict__ fluid_cell, const int3
 
 }  // namespace
 
+// Referenced planes (lbm_internal.h): plane z of a part is referenced when
+// planes z-1, z and z+1 are fully fluid and every tile that holds one of
+// their cells is dense, so that every cell reading or writing a slot of the
+// plane knows the plane.  A dense tile uses reference populations when one of
+// the planes of its cells or their neighbour planes is referenced; it then
+// gets {global plane of its first cell, first fluid index of the next plane}.
+// Only parts whose planes hold at least a tile of cells qualify (a tile then
+// spans at most two planes).
+static void mark_reference_planes(Solver &s, const std::vector<int2> &desc, const std::vector<int32_t> &poff,
+                                  std::vector<int2> &tref)
+{
+    for (const Part &P : s.parts) {
+        const int nz = P.box.nz;
+        const int64_t plane = (int64_t)P.box.nx * P.box.ny;
+        if (plane < kBlock || P.n_fluid == 0) continue;
+        const int32_t *po = poff.data() + P.poff_base;
+        std::vector<uint8_t> cov((size_t)nz, 0), refd((size_t)nz, 0);
+        for (int z = 0; z < nz; ++z) {
+            const int32_t b = po[z], e = po[z + 1];
+            if ((int64_t)(e - b) != plane) continue;
+            bool all = true;
+            for (int32_t t = b / kBlock; t <= (e - 1) / kBlock && all; ++t) all = desc[(size_t)t].x >= 0;
+            cov[(size_t)z] = all;
+        }
+        for (int z = 1; z + 1 < nz; ++z) {
+            refd[(size_t)z] = cov[(size_t)z - 1] && cov[(size_t)z] && cov[(size_t)z + 1];
+            s.plane_referenced[(size_t)(P.plane_base + z)] = refd[(size_t)z];
+        }
+        const int32_t t0 = P.fluid_off / kBlock, t1 = (P.fluid_off + P.n_fluid - 1) / kBlock;
+        for (int32_t t = t0; t <= t1; ++t) {
+            const int2 d = desc[(size_t)t];
+            if (d.x < 0) continue;
+            // planes of the tile's first and last cell
+            const int32_t first = t * kBlock, last = first + kBlock - 1;
+            const int z0 = (int)(std::upper_bound(po, po + nz + 1, first) - po) - 1;
+            const int z1 = (int)(std::upper_bound(po, po + nz + 1, last) - po) - 1;
+            bool touch = false;
+            for (int z = std::max(z0 - 1, 0); z <= std::min(z1 + 1, nz - 1); ++z) touch |= refd[(size_t)z] != 0;
+            if (touch) tref[(size_t)t] = make_int2(P.plane_base + z0, po[z0 + 1]);
+        }
+    }
+}
+
 #define LBM_CUDA_TRY(x)                                     \
     do {                                                    \
         if ((x) != cudaSuccess) return LBM_ECUDA;           \
@@ -410,7 +454,9 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     {
         // the span of dense tiles, for the odd step's dense kernel
         std::vector<int2> desc((size_t)(s.n_pad / kBlock));
+        std::vector<int32_t> poff((size_t)(s.lay.n_planes + s.parts.size()));
         LBM_CUDA_TRY(cudaMemcpyAsync(desc.data(), s.tile_desc, sizeof(int2) * desc.size(), cudaMemcpyDeviceToHost, st));
+        LBM_CUDA_TRY(cudaMemcpyAsync(poff.data(), s.plane_off, sizeof(int32_t) * poff.size(), cudaMemcpyDeviceToHost, st));
         LBM_CUDA_TRY(cudaStreamSynchronize(st));
         s.dense_lo = s.dense_hi = 0;
         for (size_t t = 0; t < desc.size(); ++t)
@@ -418,6 +464,24 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
                 if (s.dense_hi == 0) s.dense_lo = (int32_t)t;
                 s.dense_hi = (int32_t)t + 1;
             }
+        // reference planes and the tiles that use them (see lbm_internal.h)
+        std::vector<int2> tref(desc.size(), make_int2(-1, 0));
+        s.plane_referenced.assign((size_t)s.lay.n_planes, 0);
+        mark_reference_planes(s, desc, poff, tref);
+        s.ref_lo = s.ref_hi = 0;
+        for (size_t t = 0; t < tref.size(); ++t)
+            if (tref[t].x >= 0) {
+                if (s.ref_hi == 0) s.ref_lo = (int32_t)t;
+                s.ref_hi = (int32_t)t + 1;
+            }
+        s.has_ref = s.ref_hi > s.ref_lo;
+        LBM_CUDA_TRY(cudaMemcpyAsync(s.tile_ref, tref.data(), sizeof(int2) * tref.size(), cudaMemcpyHostToDevice, st));
+        LBM_CUDA_TRY(cudaMemcpyAsync(s.plane_flag, s.plane_referenced.data(), s.plane_referenced.size(),
+                                     cudaMemcpyHostToDevice, st));
+        LBM_CUDA_TRY(cudaMemsetAsync(s.ref, 0, sizeof(float) * kRefStride * (size_t)s.lay.n_planes, st));
+        LBM_CUDA_TRY(cudaMemsetAsync(s.ref_next, 0, sizeof(float) * kRefStride * (size_t)s.lay.n_planes, st));
+        // the host vectors must outlive their (pageable) copies
+        LBM_CUDA_TRY(cudaStreamSynchronize(st));
     }
     LBM_CUDA_TRY(cudaStreamSynchronize(st));
     for (size_t b = 0; b < s.parts.size(); ++b)

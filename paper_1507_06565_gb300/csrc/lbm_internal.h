@@ -17,6 +17,23 @@
 //   cell_xr    [n_pad]      uint32 x | (row << x_bits), row = y + ny z
 //   u_cur/u_prev [3][n_pad] float velocity snapshots (fluid order), rho_cur [n_pad]
 //                           holds rho - 1
+//   ref, ref_next [n_planes][kRefStride] float reference populations of the
+//                           referenced planes (see below), zero elsewhere
+//   tile_ref   [n_pad/256]  int2 {global plane of the tile's first cell, fluid
+//                           index where the next plane starts} for tiles that
+//                           use reference populations, {-1, 0} otherwise
+//
+// Reference populations.  In a fully fluid plane far from the porous layer
+// the flow is the same at every cell, so FP32 rounding of the stored
+// populations is the same at every cell of the plane and does not average
+// out: it acts like a spurious body force of up to ~2^-24 |f| per step.  In
+// such planes the slot A[.][y] of a population of direction k (owner cell y
+// in plane z) stores f_k - w_k - R_k(z), where R_k(z) = f_k^eq(1, u_z) - w_k
+// is the equilibrium of the plane's mean velocity u_z (refreshed by
+// lbm_recenter), which leaves only the small non-equilibrium part to round.
+// A plane is referenced when it and both neighbour planes lie entirely in
+// dense tiles (every cell that reads or writes its slots then knows its
+// plane); everywhere else R = 0 and the storage is the plain shifted one.
 // Links of a cell are stored in increasing k; cells in fluid order, so the
 // first link of cell i is warp_off[i/32] + (links of cells i&~31 .. i-1).
 #pragma once
@@ -40,6 +57,7 @@ constexpr int kBinEdge = 8;   // edge (cells) of the sphere-image bins
 // Eq. (CLI) (stability in sharp corners, with the two-cell-gap rule of
 // k_links).
 constexpr double kCliQmin = 0.1;
+constexpr int kRefStride = 20;   // floats per plane of reference populations (19 used)
 
 // ---------------------------------------------------------------------------
 // D3Q19 velocity set (ordering documented in lbm.h).
@@ -111,7 +129,7 @@ struct Part {
 struct Layout {
     size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr, tile_desc;
     size_t u_cur, u_prev, rho_cur, prof_prev, bins_start, bins_img, scan_tmp, partials, result, total;
-    size_t part_shift, part_foff, status;
+    size_t part_shift, part_foff, status, ref, ref_next, tile_ref, plane_flag;
     // build-time aliases inside the pdf region
     size_t idx_map, mask;
     int32_t n_pad;
@@ -177,6 +195,16 @@ struct Solver {
     // indices are then arithmetic and it has no wall link), else {-1, 0}
     int2 *tile_desc = nullptr;
     int32_t dense_lo = 0, dense_hi = 0;   // tiles [dense_lo, dense_hi) hold every dense tile
+    // reference populations (see the layout notes): per plane of all parts,
+    // the current ones and those the next step switches to
+    float *ref = nullptr;
+    float *ref_next = nullptr;
+    int2 *tile_ref = nullptr;
+    int32_t ref_lo = 0, ref_hi = 0;       // tiles [ref_lo, ref_hi) hold every tile with tile_ref.x >= 0
+    std::vector<uint8_t> plane_referenced;   // per global plane (host copy)
+    uint8_t *plane_flag = nullptr;        // the same on the device
+    bool has_ref = false;                 // some plane is referenced
+    bool ref_pending = false;             // the next step reads with ref and writes with ref_next
     uint2 *row_words = nullptr;
     uint32_t *cell_xr = nullptr;
     float *u_cur = nullptr;
@@ -224,6 +252,7 @@ int launch_residual(Solver &s);                            // -> res_field
 int launch_profile_residual(Solver &s);                    // -> part slots [1..3]
 int launch_mass(Solver &s);                                // -> res_mass, part slots [4..5]
 int launch_populations(Solver &s, float *out);
+int launch_reference_update(Solver &s);                    // u_cur -> ref_next
 
 // ---- shared host helpers ----
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

@@ -135,6 +135,19 @@ __device__ __forceinline__ void apply_shift(float h[kQ], float c)
 // Constants of a solver (defined in lbm_step.cu).
 Coef make_coef(const Solver &s);
 
+// Offset of the reference row of cell i's plane (lbm_internal.h), or -1 when
+// its tile stores no reference populations (REF: the solver has referenced
+// planes at all).  A holds tile_ref, ref_lo and ref_hi.
+template <bool REF, typename A>
+__device__ __forceinline__ int32_t ref_row(const A &p, int32_t i)
+{
+    if (!REF) return -1;
+    const int32_t tile = i / kBlock;
+    if (tile < p.ref_lo || tile >= p.ref_hi) return -1;
+    const int2 tr = __ldg(p.tile_ref + tile);
+    return tr.x < 0 ? -1 : (tr.x + (i >= tr.y ? 1 : 0)) * kRefStride;
+}
+
 // First link index of cell i and its link mask.  Must be called by all 32
 // lanes of a warp with lanes mapped to the aligned cells 32w .. 32w+31; m is
 // this lane's mask (0 for padding lanes).

@@ -33,6 +33,10 @@ struct PostArgs {
     const uint32_t *warp_off;
     const float *link_a;
     int32_t n_fluid, n_pad;
+    const int2 *tile_ref;
+    int32_t ref_lo, ref_hi;
+    const float *ref;
+    float unscale;   // storage units -> populations (FP16 stores x 2^14)
     Coef c;
 };
 
@@ -51,6 +55,14 @@ __device__ __forceinline__ bool current_populations(const T *pdf, const PostArgs
     load_links(a, m, p.link_a, off);
     if (ODD) gather_odd(h, pdf, n_pad, i, nb);
     else gather_even(h, pdf, n_pad, i);
+    // reference populations of the slots' owners: the cell itself (even
+    // time) or x - e_k (odd time, plane z - ez_k); dense tiles have no links
+    const int32_t rr = ref_row<true>(p, i);
+    if (rr >= 0) {
+#pragma unroll
+        for (int k = 0; k < kQ; ++k)
+            h[k] = __fadd_rn(h[k], __ldg(p.ref + rr - (ODD ? ez(k) : 0) * kRefStride + k) * p.unscale);
+    }
     cli_incoming(h, a);
     return true;
 }
@@ -208,6 +220,55 @@ __global__ void __launch_bounds__(kRedThreads) k_profile_residual(const double *
     }
 }
 
+// Reference populations of the planes of one part from the current mean
+// velocity of each referenced plane (u in fluid order, fresh from the
+// moments kernel): R_k = f_k^eq(1, u_z) - w_k in storage units, zero rows for
+// the other planes.  One block per plane.
+__global__ void __launch_bounds__(kRedThreads) k_reference_update(const float *__restrict__ u, int32_t n_pad,
+                                                                  const int32_t *__restrict__ plane_off,
+                                                                  int32_t plane_base,
+                                                                  const uint8_t *__restrict__ plane_flag, float scale,
+                                                                  float *__restrict__ ref_next)
+{
+    __shared__ double mean[3];
+    const int z = blockIdx.x;
+    const int32_t gp = plane_base + z;
+    float *out = ref_next + (size_t)gp * kRefStride;
+    if (!plane_flag[gp]) {   // uniform over the block
+        if (threadIdx.x < kRefStride) out[threadIdx.x] = 0.0f;
+        return;
+    }
+    const int32_t b = plane_off[z], e = plane_off[z + 1];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int32_t i = b + threadIdx.x; i < e; i += kRedThreads) {
+        sx += (double)u[i];
+        sy += (double)u[(size_t)n_pad + i];
+        sz += (double)u[2 * (size_t)n_pad + i];
+    }
+    sx = block_sum(sx);
+    sy = block_sum(sy);
+    sz = block_sum(sz);
+    if (threadIdx.x == 0) {
+        const double n = (double)(e - b);
+        mean[0] = sx / n;
+        mean[1] = sy / n;
+        mean[2] = sz / n;
+    }
+    __syncthreads();
+    const int k = threadIdx.x;
+    if (k < kRefStride) {
+        double r = 0.0;
+        if (k < kQ) {
+            const double eu = ex(k) * mean[0] + ey(k) * mean[1] + ez(k) * mean[2];
+            const double uu = mean[0] * mean[0] + mean[1] * mean[1] + mean[2] * mean[2];
+            r = weight(k) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu) * (double)scale;
+        }
+        out[k] = (float)r;
+    }
+}
+
+float storage_scale(const Solver &s) { return s.params.storage == LBM_F16 ? 16384.0f : 1.0f; }
+
 PostArgs make_post(const Solver &s)
 {
     PostArgs p;
@@ -217,6 +278,11 @@ PostArgs make_post(const Solver &s)
     p.link_a = s.link_a;
     p.n_fluid = s.n_fluid;
     p.n_pad = s.n_pad;
+    p.tile_ref = s.tile_ref;
+    p.ref_lo = s.ref_lo;
+    p.ref_hi = s.ref_hi;
+    p.ref = s.ref;
+    p.unscale = 1.0f / storage_scale(s);
     p.c = make_coef(s);
     return p;
 }
@@ -337,6 +403,17 @@ int launch_mass(Solver &s)
         k_reduce_partials<<<1, kRedThreads, 0, s.stream>>>(s.partials, np, s.result + res_part(s.lay, (int)b) + 4);
     }
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+int launch_reference_update(Solver &s)
+{
+    if (!s.has_ref) return LBM_OK;
+    for (const Part &P : s.parts)
+        k_reference_update<<<(unsigned)P.box.nz, kRedThreads, 0, s.stream>>>(
+            s.u_cur, s.n_pad, s.plane_off + P.poff_base, P.plane_base, s.plane_flag, storage_scale(s), s.ref_next);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    s.ref_pending = true;
+    return LBM_OK;
 }
 
 int residual_partial_count(int64_t n_fluid)

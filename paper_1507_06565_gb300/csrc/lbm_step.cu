@@ -56,6 +56,13 @@ struct StepArgs {
     const int32_t *part_foff;  // [n_parts + 1] first fluid index of each part
     int32_t n_parts;
     int32_t shift_on;          // apply part_shift in this launch
+    // reference populations (lbm_internal.h): tiles [ref_lo, ref_hi) may use
+    // them; slots are read relative to ref_rd and written relative to ref_wr
+    // (the same array except in the step that switches to new references)
+    const int2 *tile_ref;
+    int32_t ref_lo, ref_hi;
+    const float *ref_rd;
+    const float *ref_wr;
     Coef c;
 };
 
@@ -76,21 +83,34 @@ __device__ __forceinline__ float part_shift_of(const StepArgs<T> &p, int32_t i)
 // read where they are used, before and after the collision; the second read
 // hits L1.  Holding no staging buffer keeps shared memory free for L1 and the
 // register count at 40, so six blocks fit on an SM.
-template <typename T>
+// With reference populations (REF, a tile in or next to referenced planes),
+// the population of direction k is read as slot + R_k(z) and written as
+// f~_k - R_k(z), z the plane of the slot's owner (the cell itself in the even
+// step).  Dense tiles have no wall links.
+template <typename T, bool REF>
 __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 {
     const bool live = i < p.n_fluid;
     const uint32_t m = live ? p.lmask[i] : 0u;
     const uint32_t off = first_link(p.warp_off, i, m);
     if (!live) return;
+    const int32_t rr = ref_row<REF>(p, i);
     const size_t n_pad = (size_t)p.n_pad;
     float h[kQ];
 #pragma unroll
     for (int k = 0; k < kQ; ++k) h[k] = ld_raw(p.pdf + k * n_pad + i);
+    if (REF && rr >= 0) {
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) h[k] = __fadd_rn(h[k], __ldg(p.ref_rd + rr + k));
+    }
     if (m) cli_links<true>(h, p.link_a, off, m);
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
     if (m) cli_links<false>(h, p.link_a, off, m);
+    if (REF && rr >= 0) {
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) h[k] = __fsub_rn(h[k], __ldg(p.ref_wr + rr + k));
+    }
 #pragma unroll
     for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
 }
@@ -103,7 +123,7 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 // coefficients are read where they are used, before and after the collision
 // (the second read hits L1).
 // NB: where the neighbour indices come from (NbSource).
-template <typename T, int NB>
+template <typename T, int NB, bool REF>
 __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock])
 {
     const int t = threadIdx.x;
@@ -137,19 +157,31 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     h[0] = ld_raw(p.pdf + ui);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) h[k] = ld_raw(p.pdf + slot(opp(k)));   // A[opp k][x - e_k]
+    // reference rows: the slot read for h_k belongs to x - e_k (plane z - ez_k),
+    // the slot written with h_k to x + e_k (plane z + ez_k)
+    const int32_t rr = ref_row<REF>(p, i);
+    if (REF && rr >= 0) {
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) h[k] = __fadd_rn(h[k], __ldg(p.ref_rd + rr - ez(k) * kRefStride + k));
+    }
     if (m) cli_links<true>(h, p.link_a, off, m);
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
     if (m) cli_links<false>(h, p.link_a, off, m);
+    if (REF && rr >= 0) {
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) h[k] = __fsub_rn(h[k], __ldg(p.ref_wr + rr + ez(k) * kRefStride + k));
+    }
     st_raw(p.pdf + ui, h[0]);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) st_raw(p.pdf + slot(k), h[k]);
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, bool REF>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_even(StepArgs<T> p)
 {
-    for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x) even_cell(p, tile * kBlock + threadIdx.x);
+    for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x)
+        even_cell<T, REF>(p, tile * kBlock + threadIdx.x);
 }
 
 // Even step with the populations staged through shared memory.  A persistent
@@ -170,7 +202,7 @@ constexpr size_t even_bulk_smem()
     return (size_t)S * kQ * kBlock * sizeof(T) + (size_t)S * sizeof(uint64_t);
 }
 
-template <typename T, int S, int MINB>
+template <typename T, int S, int MINB, bool REF>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -211,10 +243,19 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
         if (__syncthreads_or(!ok)) break;   // the stage is free again
         if (t < 32 && j + S < count) issue(j + S);
         if (!live) continue;
+        const int32_t rr = ref_row<REF>(p, i);
+        if (REF && rr >= 0) {
+#pragma unroll
+            for (int k = 0; k < kQ; ++k) h[k] = __fadd_rn(h[k], __ldg(p.ref_rd + rr + k));
+        }
         if (m) cli_links<true>(h, p.link_a, off, m);
         if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
         collide(h, p.c);
         if (m) cli_links<false>(h, p.link_a, off, m);
+        if (REF && rr >= 0) {
+#pragma unroll
+            for (int k = 0; k < kQ; ++k) h[k] = __fsub_rn(h[k], __ldg(p.ref_wr + rr + k));
+        }
 #pragma unroll
         for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
     }
@@ -242,12 +283,12 @@ __global__ void k_wait_selftest(int *status, int max_polls)
     if (!ok && threadIdx.x == 0) atomicExch(status, 1);
 }
 
-template <typename T, int NB, int MINB>
+template <typename T, int NB, int MINB, bool REF>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
 {
     __shared__ int32_t nb_s[kQ - 1][kBlock];
     for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x)
-        odd_cell<T, NB>(p, tile * kBlock + threadIdx.x, nb_s);
+        odd_cell<T, NB, REF>(p, tile * kBlock + threadIdx.x, nb_s);
 }
 
 // Initial state f_k = f_k^eq(rho = 1, u0) (Eq. (equilibrium)) stored shifted
@@ -308,6 +349,11 @@ StepArgs<T> make_args(const Solver &s)
     p.part_foff = s.part_foff;
     p.n_parts = (int32_t)s.parts.size();
     p.shift_on = 0;
+    p.tile_ref = s.tile_ref;
+    p.ref_lo = s.ref_lo;
+    p.ref_hi = s.ref_hi;
+    p.ref_rd = s.ref;
+    p.ref_wr = s.ref;
     p.c.omega_p = (float)s.omega_p;
     p.c.omega_m = (float)s.omega_m;
     // storage units: the scale (a power of two) multiplies F_k and divides
@@ -346,32 +392,41 @@ struct EvenBulk<__nv_bfloat16> {
 };
 
 // The staged even step on one wave of resident blocks.
-template <typename T, int S, int MINB>
+template <typename T, int S, int MINB, bool REF>
 void launch_even_bulk(const StepArgs<T> &p, cudaStream_t st)
 {
     constexpr size_t smem = even_bulk_smem<T, S>();
     static const int wave = [] {
-        cudaFuncSetAttribute(k_step_even_bulk<T, S, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_step_even_bulk<T, S, MINB, REF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_even_bulk<T, S, MINB>, kBlock, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_even_bulk<T, S, MINB, REF>, kBlock, smem) !=
             cudaSuccess)
             nb = 1;
         return sm_count() * std::max(nb, 1);
     }();
-    k_step_even_bulk<T, S, MINB><<<(unsigned)std::min(wave, p.n_tiles), kBlock, smem, st>>>(p);
+    k_step_even_bulk<T, S, MINB, REF><<<(unsigned)std::min(wave, p.n_tiles), kBlock, smem, st>>>(p);
 }
 
 // One step launch at the current parity with the chosen grid (0: a block per
-// tile; kGridBulk: the staged even step).
+// tile; kGridBulk: the staged even step).  Solvers with referenced planes run
+// the kernels compiled with reference populations.
+template <typename T, bool REF>
+void launch_step_ref(const Solver &s, const StepArgs<T> &p, bool odd, int grid, cudaStream_t st)
+{
+    const unsigned g = (unsigned)(grid > 0 ? std::min(grid, p.n_tiles) : p.n_tiles);
+    if (!odd && grid == kGridBulk) launch_even_bulk<T, EvenBulk<T>::S, EvenBulk<T>::MINB, REF>(p, st);
+    else if (!odd) k_step_even<T, kEvenBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
+    else if (s.odd_rows) k_step_odd<T, kNbRows, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
+    else if (p.dense_hi > p.dense_lo) k_step_odd<T, kNbDense, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
+    else k_step_odd<T, kNbTable, kOddBlocksPerSM, false><<<g, kBlock, 0, st>>>(p);
+}
+
 template <typename T>
 void launch_step(const Solver &s, const StepArgs<T> &p, bool odd, int grid, cudaStream_t st)
 {
-    const unsigned g = (unsigned)(grid > 0 ? std::min(grid, p.n_tiles) : p.n_tiles);
-    if (!odd && grid == kGridBulk) launch_even_bulk<T, EvenBulk<T>::S, EvenBulk<T>::MINB>(p, st);
-    else if (!odd) k_step_even<T, kEvenBlocksPerSM><<<g, kBlock, 0, st>>>(p);
-    else if (s.odd_rows) k_step_odd<T, kNbRows, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
-    else if (p.dense_hi > p.dense_lo) k_step_odd<T, kNbDense, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
-    else k_step_odd<T, kNbTable, kOddBlocksPerSM><<<g, kBlock, 0, st>>>(p);
+    if (s.has_ref) launch_step_ref<T, true>(s, p, odd, grid, st);
+    else launch_step_ref<T, false>(s, p, odd, grid, st);
 }
 
 // Candidate schedules: a block per tile, or 1, 2, 4 waves of resident blocks
@@ -408,10 +463,23 @@ int run_steps(Solver &s, int64_t n)
     if (s.tune_state == 0) start_tuning(s, p.n_tiles);
     const int Ce = (int)s.tune_grids_even.size(), Co = (int)s.tune_grids_odd.size();
     int64_t t = 0;
+    const size_t ref_bytes = sizeof(float) * kRefStride * (size_t)s.lay.n_planes;
     while (t < n) {
         const bool odd = (s.steps & 1) != 0;
         p.shift_on = s.shift_pending ? 1 : 0;
         s.shift_pending = false;
+        // a step that switches to new reference populations reads with the
+        // old ones and writes with the new ones, which then become current
+        const bool ref_switch = s.ref_pending;
+        s.ref_pending = false;
+        p.ref_wr = ref_switch ? s.ref_next : s.ref;
+        auto after_switch = [&]() -> int {
+            if (!ref_switch) return LBM_OK;
+            p.ref_wr = s.ref;
+            return cudaMemcpyAsync(s.ref, s.ref_next, ref_bytes, cudaMemcpyDeviceToDevice, s.stream) == cudaSuccess
+                       ? LBM_OK
+                       : LBM_ECUDA;
+        };
         if (s.tune_state == 1) {
             int &cnt = odd ? s.tune_count_odd : s.tune_count_even;
             const std::vector<int> &grids = odd ? s.tune_grids_odd : s.tune_grids_even;
@@ -428,6 +496,7 @@ int run_steps(Solver &s, int64_t n)
             } else {
                 launch_step(s, p, odd, odd ? s.grid_odd : s.grid_even, s.stream);
             }
+            if (after_switch() != LBM_OK) return LBM_ECUDA;
             if (s.tune_count_even >= Ce * kTuneReps && s.tune_count_odd >= Co * kTuneReps) {
                 s.grid_even = s.tune_grids_even[std::min_element(s.tune_ms_even.begin(), s.tune_ms_even.end()) -
                                                 s.tune_ms_even.begin()];
@@ -440,7 +509,7 @@ int run_steps(Solver &s, int64_t n)
             continue;
         }
         // replay whole graph chunks from an even step, once the schedule is fixed
-        if (s.use_graph && !odd && !p.shift_on && n - t >= kGraphSteps) {
+        if (s.use_graph && !odd && !p.shift_on && !ref_switch && n - t >= kGraphSteps) {
             if (!s.graph_exec) {
                 if (!s.cap_stream && cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
                     return LBM_ECUDA;
@@ -457,6 +526,7 @@ int run_steps(Solver &s, int64_t n)
             continue;
         }
         launch_step(s, p, odd, odd ? s.grid_odd : s.grid_even, s.stream);
+        if (after_switch() != LBM_OK) return LBM_ECUDA;
         ++s.steps;
         ++t;
     }
@@ -468,7 +538,11 @@ int run_init(Solver &s, const float *u0)
 {
     s.steps = 0;
     s.shift_pending = false;
+    s.ref_pending = false;
     if (s.n_fluid == 0) return LBM_OK;
+    // the initial state is stored without reference populations
+    if (cudaMemsetAsync(s.ref, 0, sizeof(float) * kRefStride * (size_t)s.lay.n_planes, s.stream) != cudaSuccess)
+        return LBM_ECUDA;
     const StepArgs<T> p = make_args<T>(s);
     k_init<T><<<(unsigned)(s.n_pad / kBlock), kBlock, 0, s.stream>>>(p, s.fluid_cell, u0, s.n_cells);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;

@@ -21,10 +21,16 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import BatchSolver, Solver, UNet, lbm_geometry_from_spheres, lbm_sdf
+from . import LBM_FLAG_CLI_SAFEGUARDS, BatchSolver, Solver, UNet, lbm_geometry_from_spheres, lbm_sdf
 from .workloads import Channel, unet_init
 
 SDF_TRUNC = 8.0
+# Wall rule of every run here: Eq. (CLI) with the corner safeguards.  These
+# r = 4 packings hold corners where the paper's rule has modes that barely
+# decay; a warm start (a field with errors everywhere) excites them and then
+# needs more steps to the 1e-8 profile residual than a start from rest
+# (measured: 280,000 vs 104,500 steps over six held-out 32x32x64 channels).
+WALL_FLAGS = LBM_FLAG_CLI_SAFEGUARDS
 
 
 def channel_case(seed: int, shape=(64, 64, 128)) -> Channel:
@@ -52,14 +58,14 @@ class Dataset:
     seconds: float
 
 
-def generate(seeds, shape=(64, 64, 128), tol=1e-6, interval=500, max_steps=400_000) -> Dataset:
+def generate(seeds, shape=(64, 64, 128), tol=1e-6, interval=500, max_steps=400_000, flags=WALL_FLAGS) -> Dataset:
     """Steady fields of the seeded packings, all solved in one batch."""
     import torch
 
     cases = [channel_case(s, shape) for s in seeds]
     geoms = [lbm_geometry_from_spheres(*c.sphere_args()) for c in cases]
     c0 = cases[0]
-    solver = BatchSolver(geoms, c0.tau, c0.lam, c0.g)
+    solver = BatchSolver(geoms, c0.tau, c0.lam, c0.g, flags=flags)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rc, steps, res = solver.run_until(tol, interval, max_steps, criterion="profile")
@@ -127,7 +133,8 @@ def predict(params, case: Channel, geom=None):
     return u[0]
 
 
-def time_to_steady(case: Channel, u0=None, tol=1e-8, interval=500, max_steps=2_000_000, geom=None) -> dict:
+def time_to_steady(case: Channel, u0=None, tol=1e-8, interval=500, max_steps=2_000_000, geom=None,
+                   flags=WALL_FLAGS) -> dict:
     """Run one case to the plane-profile tolerance from rest (u0 None) or from
     a predicted field; wall time includes the solver set-up."""
     import torch
@@ -135,7 +142,7 @@ def time_to_steady(case: Channel, u0=None, tol=1e-8, interval=500, max_steps=2_0
     geom = geom or lbm_geometry_from_spheres(*case.sphere_args())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s = Solver(geom, case.tau, case.lam, case.g, u0=u0)
+    s = Solver(geom, case.tau, case.lam, case.g, u0=u0, flags=flags)
     rc, steps, res = s.run_until(tol, interval, max_steps, criterion="profile")
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0

@@ -165,7 +165,8 @@ def test_warm_start_gains_over_cold_start(torch_cuda):
     the steady velocity of held-out packings to within 30% (L2) where the
     cold start (rest) is 100% away; warm-started from it, the LBM reaches the
     same steady state (plane-profile residual 1e-8, permeability within 1e-3
-    of the cold start's) in fewer steps in total over six held-out packings.
+    of the cold start's) in fewer steps in total over six held-out packings
+    (wall rule with the corner safeguards, as the surrogate module runs it).
     (Training uses float atomics in the weight gradient, so single cases vary
     by a few residual intervals from run to run; the totals do not.)"""
     from paper_1507_06565_gb300 import surrogate as S
@@ -179,7 +180,7 @@ def test_warm_start_gains_over_cold_start(torch_cuda):
     for sd in range(600000, 600006):
         case = S.channel_case(sd, shape)
         geom = L.lbm_geometry_from_spheres(*case.sphere_args())
-        cold = L.Solver(geom, case.tau, case.lam, case.g)
+        cold = L.Solver(geom, case.tau, case.lam, case.g, flags=S.WALL_FLAGS)
         rc, n_cold, _ = cold.run_until(1e-8, 500, 2_000_000, criterion="profile")
         assert rc == 0
         _, u_conv = cold.moments()
@@ -187,7 +188,7 @@ def test_warm_start_gains_over_cold_start(torch_cuda):
         fl = torch_cuda.from_numpy(geom.mask() == 0).to(u0.device)   # lbm_init ignores solid cells
         err = float((u0 - u_conv)[:, fl].norm() / u_conv[:, fl].norm())
         assert err < 0.3, (sd, err)
-        warm = L.Solver(geom, case.tau, case.lam, case.g, u0=u0)
+        warm = L.Solver(geom, case.tau, case.lam, case.g, u0=u0, flags=S.WALL_FLAGS)
         rc, n_warm, _ = warm.run_until(1e-8, 500, 2_000_000, criterion="profile")
         assert rc == 0
         window = (2, case.nz // 2 - 8)
