@@ -209,14 +209,18 @@ def workload_name(args):
 # --wall-rule auto these run with the corner safeguards
 # (LBM_FLAG_CLI_SAFEGUARDS), every other packing with the paper's rule.  A
 # batch takes the safeguards when any of its boxes needs them.
-PAPER_CLI_UNSTABLE = {"W2 256x256x512 r=8 phi=0.4", "W4 cube 5 edge=149", "W4 cube 17 edge=151",
-                      "W4 cube 47 edge=52"}
+PAPER_CLI_UNSTABLE = {"W2 256x256x512 r=8 phi=0.4", "W3 512x512x1024 r=8 phi=0.6", "W4 cube 5 edge=149",
+                      "W4 cube 17 edge=151", "W4 cube 47 edge=52"}
+# workloads that always take the safeguards: the REV batch (cubes 5 and 17
+# grow), the warm-start channels (held-out channel 600006 diverges) and the
+# resolution studies (their D = 4 packing diverges under flow)
+SAFEGUARDED_WORKLOADS = ("rev", "surrogate", "grid-study", "re-sweep")
 
 
 def wall_rule(args, cases=()) -> str:
     rule = getattr(args, "wall_rule", "auto")
     if rule == "auto":
-        if getattr(args, "workload", "channel") in ("rev", "surrogate"):
+        if getattr(args, "workload", "channel") in SAFEGUARDED_WORKLOADS:
             return "safeguards"
         rule = "safeguards" if any(c.name in PAPER_CLI_UNSTABLE for c in cases) else "paper"
     return rule
@@ -227,8 +231,8 @@ def odd_flags(args, cases=()) -> int:
     bounce-back or staged even step, and the wall rule for these packings."""
     import paper_1507_06565_gb300 as L
 
-    flags = {"auto": 0, "table": L.LBM_FLAG_NEIGHBOUR_TABLE,
-             "rows": L.LBM_FLAG_ROW_NEIGHBOURS}[getattr(args, "odd", "auto")]
+    flags = {"auto": 0, "table": L.LBM_FLAG_NEIGHBOUR_TABLE, "rows": L.LBM_FLAG_ROW_NEIGHBOURS,
+             "staged": L.LBM_FLAG_STAGED_NEIGHBOURS}[getattr(args, "odd", "auto")]
     if getattr(args, "bounce_back", False):
         flags |= L.LBM_FLAG_SIMPLE_BOUNCE_BACK
     if getattr(args, "even", "auto") == "staged":
@@ -882,8 +886,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--odd", choices=["auto", "table", "rows"], default="auto",
-                    help="neighbour indices of the odd step (library default, int32 table, row bitmasks)")
+    ap.add_argument("--odd", choices=["auto", "table", "rows", "staged"], default="auto",
+                    help="neighbour indices of the odd step (library default, int32 table, row bitmasks, row words "
+                         "staged per tile)")
     ap.add_argument("--even", choices=["auto", "staged"], default="auto",
                     help="even-step kernel: autotuned, or always the TMA-staged one")
     ap.add_argument("--bounce-back", action="store_true",

@@ -107,6 +107,14 @@ typedef struct {
  * 32 bits. */
 #define LBM_FLAG_NEIGHBOUR_TABLE 1
 #define LBM_FLAG_ROW_NEIGHBOURS 2
+/* Neighbour indices outside the computed tiles from the row bitmasks of the
+ * tile's rows and their neighbour rows, which each block stages in shared
+ * memory once per tile of 256 cells (about 4 bytes per cell and odd step,
+ * the cell's packed position, instead of the table's 72); cells in the
+ * first or last row of a periodic span, tiles across boxes and tiles whose
+ * rows do not fit the staging buffer use the table.  Needs nx, ny <= 2048
+ * and nz <= 1024 (else the table is used). */
+#define LBM_FLAG_STAGED_NEIGHBOURS 256
 /* Scheduling switches.  By default lbm_step times a few grid sizes for each
  * step kernel during its first launches on solvers of more than ~4 waves of
  * blocks (synchronising the stream while it does so) and then replays the
@@ -132,6 +140,16 @@ typedef struct {
  * paper's update was observed to grow without bound; the safeguards keep it
  * bounded at the price of a half-way wall on those links. */
 #define LBM_FLAG_CLI_SAFEGUARDS 128
+/* Reference equilibria in translation-invariant planes (see lbm_recenter):
+ * fully fluid planes whose neighbour planes are fully fluid store each
+ * population relative to the equilibrium of the plane's mean velocity, which
+ * lbm_recenter refreshes.  Storage rounding then acts on the small
+ * non-equilibrium part only: in FP16/BF16 storage the free-channel velocity
+ * error falls by about an order of magnitude.  It costs the step kernels one
+ * reference load and one addition per population in those planes (measured
+ * 3% of the FP32 and 7% of the FP16 step on the 256x256x512 channels), so it
+ * is off by default. */
+#define LBM_FLAG_PLANE_REFERENCES 512
 
 /* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
  * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes
@@ -293,16 +311,16 @@ int lbm_mass(lbm_solver *solver, double *mean_drho);
  * Eq. (CLI), a w - a w + w = w, all commute with it), so velocities are
  * unchanged in exact arithmetic; it keeps the stored populations small so
  * that reduced-precision storage keeps its resolution in long runs.
- * In the same way it refreshes the reference populations of the solver's
- * translation-invariant planes (fully fluid planes whose neighbour planes are
- * fully fluid too, e.g. the free channel above a porous layer): there every
- * slot stores its population minus the equilibrium f^eq(1, u_z) of the
- * plane's mean velocity, so that storage rounding acts on the small
- * non-equilibrium part only (rounding that is the same at every cell of such
- * a plane would otherwise act like a spurious body force).  The next step
- * switches to the new references; the stored values change, the populations
- * they represent do not.  *shift_out (may be NULL) receives the scheduled
- * shift.  Synchronises the stream. */
+ * With LBM_FLAG_PLANE_REFERENCES it also refreshes the reference populations
+ * of the solver's translation-invariant planes (fully fluid planes whose
+ * neighbour planes are fully fluid too, e.g. the free channel above a porous
+ * layer): there every slot stores its population minus the equilibrium
+ * f^eq(1, u_z) of the plane's mean velocity, so that storage rounding acts on
+ * the small non-equilibrium part only (rounding that is the same at every
+ * cell of such a plane would otherwise act like a spurious body force).  The
+ * next step switches to the new references; the stored values change, the
+ * populations they represent do not.  *shift_out (may be NULL) receives the
+ * scheduled shift.  Synchronises the stream. */
 int lbm_recenter(lbm_solver *solver, double *shift_out);
 
 #define LBM_CONVERGE_FIELD 0    /* lbm_residual */
@@ -332,9 +350,10 @@ int lbm_save(lbm_solver *solver, void *host_buf, size_t bytes);
 int lbm_load(lbm_solver *solver, const void *host_buf, size_t bytes);
 
 /* Number of planes (over all parts) whose slots store populations relative
- * to the plane's reference equilibrium (see lbm_recenter): fully fluid planes
- * whose neighbour planes are fully fluid and lie in tiles of 256 cells that
- * hold only such planes' cells. */
+ * to the plane's reference equilibrium (LBM_FLAG_PLANE_REFERENCES, see
+ * lbm_recenter): fully fluid planes whose neighbour planes are fully fluid
+ * and lie in tiles of 256 cells that hold only such planes' cells; 0 without
+ * the flag. */
 int lbm_reference_planes(const lbm_solver *solver, int32_t *n_planes);
 
 /* Steps taken since lbm_init/lbm_reset. */

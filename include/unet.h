@@ -79,6 +79,27 @@ int unet_backward(unet_net *net, const float *dev_target, float target_scale, do
  * then refresh of the bf16 weight copies. */
 int unet_adam_step(unet_net *net, float lr, float beta1, float beta2, float eps);
 
+/* One 3x3x3 convolution layer as the network runs it (its kernels exposed for
+ * checks and per-layer measurements): dev_y[v][o] = bf16(act(bias[o] +
+ * sum_t sum_c w[t][o][c] x[v + off_t][c])), act = ReLU when relu != 0, with
+ * fp32 accumulation on the tensor cores.  bf16 values are passed as their
+ * 16-bit patterns: activations [n][nz][ny][nx][c] (c fastest), weights
+ * dev_w[27][co][ci] (tap 9(dz+1) + 3(dy+1) + (dx+1)); dev_bias fp32 [co] or
+ * NULL.  Padding is circular in x and y and zero in z.  ci and co are
+ * multiples of 16, co <= 256, n nz ny nx < 2^31.  *dev_status (caller-owned,
+ * zero on entry) is set to 1 if a bounded device-side wait gave up.
+ * Asynchronous on `stream`. */
+int unet_conv3d(const uint16_t *dev_x, int32_t ci, const uint16_t *dev_w, const float *dev_bias, uint16_t *dev_y,
+                int32_t co, int32_t n, int32_t nz, int32_t ny, int32_t nx, int32_t relu, int32_t *dev_status,
+                void *stream);
+
+/* Weight gradient of that layer: dev_dw[t][o][c] (fp32) += sum_v
+ * dy[v][o] x[v + off_t][c] with the same padding; dy and x bf16 as above.
+ * co <= 128 and ci <= 256, multiples of 16.  Partial sums are added with fp32
+ * atomics (the order of the additions is not fixed).  Asynchronous. */
+int unet_conv3d_wgrad(const uint16_t *dev_dy, int32_t co, const uint16_t *dev_x, int32_t ci, float *dev_dw,
+                      int32_t n, int32_t nz, int32_t ny, int32_t nx, int32_t *dev_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

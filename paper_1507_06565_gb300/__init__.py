@@ -37,6 +37,8 @@ LBM_FLAG_NO_AUTOTUNE = 8
 LBM_FLAG_SIMPLE_BOUNCE_BACK = 32
 LBM_FLAG_STAGED_EVEN = 64
 LBM_FLAG_CLI_SAFEGUARDS = 128
+LBM_FLAG_STAGED_NEIGHBOURS = 256
+LBM_FLAG_PLANE_REFERENCES = 512
 
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1
@@ -150,6 +152,8 @@ SIGNATURES = {
     "unet_forward": (_I, [_P, _P, _P, ctypes.c_float]),
     "unet_backward": (_I, [_P, _P, ctypes.c_float, ctypes.POINTER(_D)]),
     "unet_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "unet_conv3d": (_I, [_P, _I32, _P, _P, _P, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P]),
+    "unet_conv3d_wgrad": (_I, [_P, _I32, _P, _I32, _P, _I32, _I32, _I32, _I32, _P, _P]),
     "lbm_solver_destroy": (None, [_P]),
     "lbm_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -659,6 +663,42 @@ class UNet:
     def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(load_library().unet_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps)),
                "unet_adam_step")
+
+
+def unet_conv3d(x, w, bias, co: int, dims, relu: bool = True, out=None, status=None, stream=None):
+    """One 3x3x3 convolution layer (include/unet.h): x bf16 [n, nz, ny, nx, ci]
+    CUDA tensor, w bf16 [27, co, ci], bias fp32 [co] or None; returns the bf16
+    output [n, nz, ny, nx, co].  ``status`` (int32 [1], zero) records a wait
+    that gave up."""
+    import torch
+
+    n, nz, ny, nx = dims
+    ci = int(x.shape[-1])
+    if out is None:
+        out = torch.empty((n, nz, ny, nx, co), dtype=torch.bfloat16, device=x.device)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device).cuda_stream
+    _check(load_library().unet_conv3d(_dev_ptr(x), ci, _dev_ptr(w), _dev_ptr(bias), _dev_ptr(out), co, n, nz, ny, nx,
+                                      int(relu), _dev_ptr(status), ctypes.c_void_p(st)), "unet_conv3d")
+    return out
+
+
+def unet_conv3d_wgrad(dy, x, dims, dw=None, status=None, stream=None):
+    """Weight gradient of a 3x3x3 layer: dw fp32 [27, co, ci] += sum_v dy[v, o]
+    x[v + off_t, c] (dy bf16 [.., co], x bf16 [.., ci])."""
+    import torch
+
+    n, nz, ny, nx = dims
+    co, ci = int(dy.shape[-1]), int(x.shape[-1])
+    if dw is None:
+        dw = torch.zeros((27, co, ci), dtype=torch.float32, device=x.device)
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device).cuda_stream
+    _check(load_library().unet_conv3d_wgrad(_dev_ptr(dy), co, _dev_ptr(x), ci, _dev_ptr(dw), n, nz, ny, nx,
+                                            _dev_ptr(status), ctypes.c_void_p(st)), "unet_conv3d_wgrad")
+    return dw
 
 
 def lbm_batch_init(geoms, **kw) -> BatchSolver:

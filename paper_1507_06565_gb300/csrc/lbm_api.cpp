@@ -25,8 +25,12 @@ Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size
         n_planes += g->box.nz;
         n_poff += g->box.nz + 1;
     }
-    const bool single = geoms.size() == 1;
-    const lbm_box &b0 = geoms[0]->box;
+    bool packable = true;
+    int64_t n_words = 0;
+    for (const Geometry *g : geoms) {
+        packable = packable && rows_packable(g->box);
+        n_words += (int64_t)g->box.ny * g->box.nz * ((g->box.nx + 31) / 32);
+    }
     const int64_t n_pad = ((n_fluid > 0 ? n_fluid : 1) + kBlock - 1) / kBlock * kBlock;
     L.n_pad = (int32_t)n_pad;
     L.n_parts = (int32_t)geoms.size();
@@ -53,8 +57,9 @@ Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size
     L.fluid_cell = take((size_t)n_pad * 4);
     L.plane_off = take((size_t)n_poff * 4);
     L.tile_desc = take((size_t)n_pad / kBlock * 8);
-    L.row_words = take(single ? (size_t)b0.ny * b0.nz * ((b0.nx + 31) / 32) * 8 : 0);
-    L.cell_xr = take(single ? (size_t)n_pad * 4 : 0);
+    L.row_words = take(packable ? (size_t)n_words * 8 : 0);
+    L.cell_xr = take(packable ? (size_t)n_pad * 4 : 0);
+    L.tile_rows = take((size_t)n_pad / kBlock * 16);
     L.u_cur = take((size_t)3 * n_pad * 4);
     L.u_prev = take((size_t)3 * n_pad * 4);
     L.rho_cur = take((size_t)n_pad * 4);
@@ -75,17 +80,9 @@ Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size
     return L;
 }
 
-int x_bits_for(int nx)
-{
-    int b = 1;
-    while ((1 << b) < nx) ++b;
-    return b;
-}
-
 bool rows_packable(const lbm_box &box)
 {
-    const int xb = x_bits_for(box.nx);
-    return (int64_t)box.ny * box.nz <= ((int64_t)1 << (32 - xb));
+    return box.nx <= (1 << kXyzBitsX) && box.ny <= (1 << kXyzBitsY) && box.nz <= (1 << kXyzBitsZ);
 }
 
 // The kernels address populations with 32-bit element offsets (19 n_pad <
@@ -109,9 +106,11 @@ static bool params_ok(const lbm_params *p)
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p->g[d])) return false;
     const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE |
-                          LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_STAGED_EVEN | LBM_FLAG_CLI_SAFEGUARDS;
+                          LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_STAGED_EVEN | LBM_FLAG_CLI_SAFEGUARDS |
+                          LBM_FLAG_STAGED_NEIGHBOURS | LBM_FLAG_PLANE_REFERENCES;
     if ((p->flags & ~known) != 0) return false;
-    if ((p->flags & LBM_FLAG_NEIGHBOUR_TABLE) && (p->flags & LBM_FLAG_ROW_NEIGHBOURS)) return false;
+    const int32_t variants = p->flags & (LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_STAGED_NEIGHBOURS);
+    if (variants & (variants - 1)) return false;   // at most one neighbour variant
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
 }
 
@@ -167,7 +166,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->stream = (cudaStream_t)stream;
     s->ws = (char *)dev_workspace;
     s->lay = L;
-    int64_t cell_base = 0;
+    int64_t cell_base = 0, words_base = 0;
     int32_t fluid_off = 0, plane_base = 0, poff_base = 0;
     for (const Geometry *g : geoms) {
         Part P;
@@ -180,7 +179,9 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
         P.n_spheres = (int64_t)(g->spheres.size() / 4);
         P.plane_base = plane_base;
         P.poff_base = poff_base;
+        P.words_base = words_base;
         s->parts.push_back(P);
+        words_base += (int64_t)g->box.ny * g->box.nz * ((g->box.nx + 31) / 32);
         cell_base += P.n_cells;
         fluid_off += P.n_fluid;
         plane_base += g->box.nz;
@@ -206,6 +207,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->row_words = (uint2 *)(s->ws + L.row_words);
     s->cell_xr = (uint32_t *)(s->ws + L.cell_xr);
     s->tile_desc = (int2 *)(s->ws + L.tile_desc);
+    s->tile_rows = (int4 *)(s->ws + L.tile_rows);
     s->u_cur = (float *)(s->ws + L.u_cur);
     s->u_prev = (float *)(s->ws + L.u_prev);
     s->rho_cur = (float *)(s->ws + L.rho_cur);
@@ -221,12 +223,14 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
     s->plane_flag = (uint8_t *)(s->ws + L.plane_flag);
     const bool single = geoms.size() == 1;
     s->n_words = (s->box.nx + 31) / 32;
-    s->x_bits = x_bits_for(s->box.nx);
+    s->rows_ok = true;   // make_layout gives every part row words and cell_xr then
+    for (const Geometry *g : geoms) s->rows_ok = s->rows_ok && rows_packable(g->box);
     {
         bool rows = false;   // auto: the table (see LBM_FLAG_* in lbm.h)
         if (params->flags & LBM_FLAG_NEIGHBOUR_TABLE) rows = false;
         if (params->flags & LBM_FLAG_ROW_NEIGHBOURS) rows = true;
-        s->odd_rows = rows && single && rows_packable(s->box);
+        s->odd_rows = rows && single && s->rows_ok;
+        s->staged_rows = (params->flags & LBM_FLAG_STAGED_NEIGHBOURS) && s->rows_ok && !s->odd_rows;
     }
     s->use_graph = !(params->flags & LBM_FLAG_NO_GRAPH);
     s->autotune = !(params->flags & LBM_FLAG_NO_AUTOTUNE);

@@ -7,7 +7,8 @@
 //   2. dense index map cell -> global fluid index (-1 solid) and fluid_cell[]
 //      (concatenated cell index);
 //   3. neighbour table nbr[k][i] and link mask lmask[i] (bit k: x + e_k solid),
-//      packed (x, row) and row bitmask words (single part only);
+//      packed positions and row bitmask words (boxes of up to 2048 x 2048 x
+//      1024 cells), and the tiles whose odd step stages row words;
 //   4. first fluid index of each z plane of the part;
 // then over the whole solver: link counts per aligned group of 32 fluid cells
 // and their exclusive scan; and again per part:
@@ -97,7 +98,8 @@ __global__ void k_fill_index(const uint8_t *__restrict__ mask, int64_t ncell,
     }
 }
 
-// Row bitmask words: one thread per (row, word) of 32 cells along x.
+// Row bitmask words of one part (idx_map holds global fluid indices): one
+// thread per (row, word) of 32 cells along x.
 __global__ void k_row_words(const int32_t *__restrict__ idx_map, int nx, int64_t nrows, int nw,
                             uint2 *__restrict__ words)
 {
@@ -124,14 +126,14 @@ __global__ void k_row_words(const int32_t *__restrict__ idx_map, int nx, int64_t
 //    part; idx_map holds global fluid indices.
 __global__ void k_neighbours(const int32_t *__restrict__ idx_map, const int32_t *__restrict__ fluid_cell,
                              int32_t begin, int32_t end, int64_t cell_base, int32_t n_pad, int nx, int ny, int nz,
-                             int periodic_z, int x_bits, int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
+                             int periodic_z, int32_t *__restrict__ nbr, uint32_t *__restrict__ lmask,
                              uint32_t *__restrict__ cell_xr)
 {
     const int32_t i = begin + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
     if (i >= end) return;
     const int32_t c = (int32_t)(fluid_cell[i] - cell_base);
     const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
-    if (cell_xr) cell_xr[i] = (uint32_t)x | ((uint32_t)(c / nx) << x_bits);
+    if (cell_xr) cell_xr[i] = (uint32_t)x | ((uint32_t)y << kXyzBitsX) | ((uint32_t)z << (kXyzBitsX + kXyzBitsY));
     uint32_t m = 0;
 #pragma unroll
     for (int k = 1; k < kQ; ++k) {
@@ -298,6 +300,30 @@ __global__ void k_plane_offsets(const int32_t *__restrict__ fluid_cell, int32_t 
         for (int zz = z + 1; zz <= nz; ++zz) plane_off[zz] = end;
 }
 
+// Staged tiles of one part (Solver::tile_rows): a tile of kBlock fluid cells
+// that lies in the part and is not dense gets the descriptor of the three
+// bands of rows its odd step stages: the rows r_first - 1 .. r_last + 1
+// (r = y + ny z) of its first and last cell, and the same rows one plane
+// below and above.  {first row word of the part, r_first - 1,
+// band_rows | nw << 8 | periodic_z << 15 | nz << 16, nx | ny << 16}; tiles
+// whose bands exceed kMaxStagedWords keep the table.
+__global__ void k_stage_tiles(const int32_t *__restrict__ fluid_cell, const int2 *__restrict__ dense,
+                              int32_t begin, int32_t end, int64_t cell_base, int nx, int ny, int nz, int periodic_z,
+                              int64_t words_base, int4 *__restrict__ out)
+{
+    const int32_t t = begin / kBlock + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int32_t first = t * kBlock, last = first + kBlock - 1;
+    if (first >= end) return;
+    if (first < begin || last >= end) return;   // straddles a part boundary or the end: table
+    if (dense[t].x >= 0) return;                 // computed indices
+    const int32_t r_first = (int32_t)((fluid_cell[first] - cell_base) / nx);
+    const int32_t r_last = (int32_t)((fluid_cell[last] - cell_base) / nx);
+    const int band_rows = r_last - r_first + 3, nw = (nx + 31) / 32;
+    if (band_rows > 255 || 3 * band_rows * nw > kMaxStagedWords) return;
+    out[t] = make_int4((int32_t)words_base, r_first - 1, band_rows | (nw << 8) | (periodic_z << 15) | (nz << 16),
+                       nx | (ny << 16));
+}
+
 // Dense tiles of one part (see Solver::tile_desc): tile t holds fluid cells
 // t*kBlock .. t*kBlock+kBlock-1; it is dense when they all belong to this part
 // and lie in planes z with 1 <= z <= nz - 2 such that planes z - 1, z, z + 1
@@ -382,11 +408,11 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     uint32_t *d_total = (uint32_t *)(s.ws + L.result);
     int32_t *d_bstart = (int32_t *)(s.ws + L.bins_start);
     SphereImage *d_img = (SphereImage *)(s.ws + L.bins_img);
-    const bool single = s.parts.size() == 1;
-    uint32_t *cell_xr = single ? s.cell_xr : nullptr;
+    uint32_t *cell_xr = s.rows_ok ? s.cell_xr : nullptr;
     std::vector<uint32_t> counts(s.parts.size() + 1, 0);
 
     LBM_CUDA_TRY(cudaMemsetAsync(s.tile_desc, 0xFF, sizeof(int2) * (s.n_pad / kBlock), st));
+    LBM_CUDA_TRY(cudaMemsetAsync(s.tile_rows, 0xFF, sizeof(int4) * (s.n_pad / kBlock), st));
     LBM_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int), st));
     for (size_t b = 0; b < s.parts.size(); ++b) {
         const Part &P = s.parts[b];
@@ -403,8 +429,8 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
         if (P.n_fluid > 0) {
             const int32_t begin = P.fluid_off, end = P.fluid_off + P.n_fluid;
             k_neighbours<<<blocks_for(P.n_fluid), kBlock, 0, st>>>(d_idx, s.fluid_cell, begin, end, P.cell_base,
-                                                                    s.n_pad, nx, ny, nz, P.box.periodic_z, s.x_bits,
-                                                                    s.nbr, s.lmask, cell_xr);
+                                                                    s.n_pad, nx, ny, nz, P.box.periodic_z, s.nbr,
+                                                                    s.lmask, cell_xr);
             k_plane_offsets<<<blocks_for(P.n_fluid), kBlock, 0, st>>>(s.fluid_cell, begin, end, P.cell_base, nx * ny,
                                                                        nz, s.plane_off + P.poff_base);
             if (nx < 65536 && ny < 32768) {
@@ -412,12 +438,19 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
                 k_dense_tiles<<<blocks_for(tiles), kBlock, 0, st>>>(s.fluid_cell, s.plane_off + P.poff_base, begin,
                                                                      end, P.cell_base, nx, ny, nz, s.tile_desc);
             }
+            if (s.staged_rows) {
+                const int32_t tiles = end / kBlock - begin / kBlock + 1;
+                k_stage_tiles<<<blocks_for(tiles), kBlock, 0, st>>>(s.fluid_cell, s.tile_desc, begin, end, P.cell_base,
+                                                                     nx, ny, nz, P.box.periodic_z, P.words_base,
+                                                                     s.tile_rows);
+            }
         } else {
             LBM_CUDA_TRY(cudaMemsetAsync(s.plane_off + P.poff_base, 0, sizeof(int32_t) * (nz + 1), st));
         }
-        if (single) {
-            const int64_t nrows = (int64_t)ny * nz, nwords = nrows * s.n_words;
-            k_row_words<<<blocks_for(nwords), kBlock, 0, st>>>(d_idx, nx, nrows, s.n_words, s.row_words);
+        if (s.rows_ok) {
+            const int nw = (nx + 31) / 32;
+            const int64_t nrows = (int64_t)ny * nz, nwords = nrows * nw;
+            k_row_words<<<blocks_for(nwords), kBlock, 0, st>>>(d_idx, nx, nrows, nw, s.row_words + P.words_base);
         }
         LBM_CUDA_TRY(cudaGetLastError());
         // the next part reuses the mask and index map: keep the order
@@ -454,8 +487,10 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
     {
         // the span of dense tiles, for the odd step's dense kernel
         std::vector<int2> desc((size_t)(s.n_pad / kBlock));
+        std::vector<int4> trows(desc.size());
         std::vector<int32_t> poff((size_t)(s.lay.n_planes + s.parts.size()));
         LBM_CUDA_TRY(cudaMemcpyAsync(desc.data(), s.tile_desc, sizeof(int2) * desc.size(), cudaMemcpyDeviceToHost, st));
+        LBM_CUDA_TRY(cudaMemcpyAsync(trows.data(), s.tile_rows, sizeof(int4) * trows.size(), cudaMemcpyDeviceToHost, st));
         LBM_CUDA_TRY(cudaMemcpyAsync(poff.data(), s.plane_off, sizeof(int32_t) * poff.size(), cudaMemcpyDeviceToHost, st));
         LBM_CUDA_TRY(cudaStreamSynchronize(st));
         s.dense_lo = s.dense_hi = 0;
@@ -464,10 +499,16 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
                 if (s.dense_hi == 0) s.dense_lo = (int32_t)t;
                 s.dense_hi = (int32_t)t + 1;
             }
+        s.rows_lo = s.rows_hi = 0;
+        for (size_t t = 0; t < trows.size(); ++t)
+            if (trows[t].x >= 0) {
+                if (s.rows_hi == 0) s.rows_lo = (int32_t)t;
+                s.rows_hi = (int32_t)t + 1;
+            }
         // reference planes and the tiles that use them (see lbm_internal.h)
         std::vector<int2> tref(desc.size(), make_int2(-1, 0));
         s.plane_referenced.assign((size_t)s.lay.n_planes, 0);
-        mark_reference_planes(s, desc, poff, tref);
+        if (s.params.flags & LBM_FLAG_PLANE_REFERENCES) mark_reference_planes(s, desc, poff, tref);
         s.ref_lo = s.ref_hi = 0;
         for (size_t t = 0; t < tref.size(); ++t)
             if (tref[t].x >= 0) {

@@ -24,7 +24,7 @@ constexpr char kMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
 constexpr uint32_t kVersion = 1;
 // flags that change the wall links or the arithmetic (the others only pick
 // kernels or schedules, which give the same bits)
-constexpr int32_t kStateFlags = LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_CLI_SAFEGUARDS;
+constexpr int32_t kStateFlags = LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_CLI_SAFEGUARDS | LBM_FLAG_PLANE_REFERENCES;
 
 struct Header {
     char magic[8];

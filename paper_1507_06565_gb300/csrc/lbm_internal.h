@@ -11,10 +11,14 @@
 //   link_q     [n_links]    double, link fraction q (kept for export)
 //   fluid_cell [n_pad]      int32 cell index c = x + nx (y + ny z)
 //   plane_off  [nz+1]       int32 first fluid index of each z plane
-//   row_words  [ny*nz][nw]  uint2 per 32-cell word of each x-row (y, z):
+//   row_words  [ny*nz][nw]  uint2 per 32-cell word of each x-row (y, z) of
+//                           every part (part b from words_base):
 //                           {fluid bitmask, fluid index of its first fluid cell};
 //                           a neighbour's index is base + popc(bits below x)
-//   cell_xr    [n_pad]      uint32 x | (row << x_bits), row = y + ny z
+//   cell_xr    [n_pad]      uint32 x | y << 11 | z << 22 (kXyz* bits)
+//   tile_rows  [n_pad/256]  int4 descriptor of a tile whose odd-step
+//                           neighbours come from row words staged in shared
+//                           memory (see k_stage_tiles), {-1, ..} otherwise
 //   u_cur/u_prev [3][n_pad] float velocity snapshots (fluid order), rho_cur [n_pad]
 //                           holds rho - 1
 //   ref, ref_next [n_planes][kRefStride] float reference populations of the
@@ -58,6 +62,12 @@ constexpr int kBinEdge = 8;   // edge (cells) of the sphere-image bins
 // k_links).
 constexpr double kCliQmin = 0.1;
 constexpr int kRefStride = 20;   // floats per plane of reference populations (19 used)
+// packed cell position x | y << 11 | z << 22 (row bitmask variants)
+constexpr int kXyzBitsX = 11, kXyzBitsY = 11, kXyzBitsZ = 10;
+// row words one tile of the odd step stages in shared memory (3 bands of
+// rows: the planes z - 1, z, z + 1 of the tile's rows and one more row on
+// either side)
+constexpr int kMaxStagedWords = 512;
 
 // ---------------------------------------------------------------------------
 // D3Q19 velocity set (ordering documented in lbm.h).
@@ -122,12 +132,14 @@ struct Part {
     int64_t n_spheres = 0;
     int32_t plane_base = 0;   // first plane of this part in the concatenated plane arrays
     int32_t poff_base = 0;    // first entry of this part in plane_off (nz + 1 per part)
+    int64_t words_base = 0;   // first row word of this part
     bool has_prev_profile = false;
 };
 
 // Workspace carve-up.
 struct Layout {
-    size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr, tile_desc;
+    size_t pdf, nbr, lmask, warp_off, warp_cnt, link_a, link_q, fluid_cell, plane_off, row_words, cell_xr, tile_desc,
+        tile_rows;
     size_t u_cur, u_prev, rho_cur, prof_prev, bins_start, bins_img, scan_tmp, partials, result, total;
     size_t part_shift, part_foff, status, ref, ref_next, tile_ref, plane_flag;
     // build-time aliases inside the pdf region
@@ -161,9 +173,10 @@ struct Solver {
     double omega_p = 0, omega_m = 0, nu = 0;
     bool shift_pending = false;    // the next step applies part_shift
     std::vector<float> shift_host; // per-part shifts (host copy)
-    int n_words = 0;               // 32-cell words per row (single part)
-    int x_bits = 0;                // bits of x in cell_xr
+    int n_words = 0;               // 32-cell words per row (part 0)
+    bool rows_ok = false;          // every part fits the packed positions: row words and cell_xr exist
     bool odd_rows = true;          // odd step computes neighbours from row bitmasks
+    bool staged_rows = false;      // odd step stages row words per tile (LBM_FLAG_STAGED_NEIGHBOURS)
     // launch schedule: grid sizes of the even/odd step (0 = one block per
     // tile, -1 = the staged even kernel on one wave of resident blocks)
     int grid_even = 0, grid_odd = 0;
@@ -207,6 +220,8 @@ struct Solver {
     bool ref_pending = false;             // the next step reads with ref and writes with ref_next
     uint2 *row_words = nullptr;
     uint32_t *cell_xr = nullptr;
+    int4 *tile_rows = nullptr;
+    int32_t rows_lo = 0, rows_hi = 0;    // tiles [rows_lo, rows_hi) hold every staged tile
     float *u_cur = nullptr;
     float *u_prev = nullptr;
     float *rho_cur = nullptr;
@@ -231,8 +246,7 @@ void build_bins(const lbm_box &box, const std::vector<double> &spheres, Bins &bi
 
 // ---- workspace (lbm_api.cpp) ----
 Layout make_layout(const std::vector<const Geometry *> &geoms, int storage, size_t n_bins, size_t n_images);
-// bits needed for x in cell_xr; rows must fit in the remaining bits
-int x_bits_for(int nx);
+// positions of the box fit the packing of cell_xr
 bool rows_packable(const lbm_box &box);
 
 // ---- device build (lbm_build.cu) ----

@@ -116,9 +116,14 @@ __device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, int max_pol
 }  // namespace bulk
 
 // Relaxation constants and source term of one solver (kernel parameter).
+// Index 0 of ep_c/em_c is the axis class (w = 1/18), 1 the diagonal class
+// (w = 1/36).
 struct Coef {
     float omega_p, omega_m;
+    float half_omega_m;  // omega- / 2
     float usq_c, eu_c;   // 3/2 and 9/2 over the storage scale (quadratic terms)
+    float ep_c[2];       // w eu_c: the quadratic term of the symmetric equilibrium
+    float em_c[2];       // 3 w omega-: the antisymmetric equilibrium, relaxed
     float force[kQ];     // F_k = 3 w_k e_k.g, times the storage scale
     float half_g[3];   // g/2, added to j for the reported velocity
 };
@@ -250,30 +255,32 @@ __device__ __forceinline__ float e_dot(int k, float jx, float jy, float jz)
 // on shifted populations: h~_k = h_k - w+ (h_k^+ - e_k^+) - w- (h_k^- - e_k^-) + F_k,
 // e_k^+ = w_k (drho + 9/2 (e.j)^2 - 3/2 j.j), e_k^- = 3 w_k e.j, with the
 // pre-collision momentum j.  h is in storage units (Coef carries the scale of
-// the quadratic terms and of F_k).  Every rounding is spelled out (fmaf, __fmul_rn,
-// __fadd_rn: the compiler may not contract or reorder them), so all step
-// kernels produce the same bits for the same inputs whatever code surrounds
-// the collision.
+// the quadratic terms and of F_k).  Pair by pair (k, kbar = k + 1 for odd k),
+// with s = h_k + h_kbar and a = h_k - h_kbar:
+//   dp = w+ (s/2 - e_k^+),   dm' = w-/2 a - (w- e_k^- + F_k),
+//   h~_k = h_k - dp - dm',   h~_kbar = h_kbar - dp + dm'.
+// Every rounding is spelled out (fmaf, __fmul_rn, __fadd_rn: the compiler may
+// not contract or reorder them), so all step kernels produce the same bits for
+// the same inputs whatever code surrounds the collision.
 __device__ __forceinline__ void collide(float h[kQ], const Coef &c)
 {
     float drho, jx, jy, jz;
     moments(h, drho, jx, jy, jz);
     const float usq = __fmul_rn(c.usq_c, fmaf(jz, jz, fmaf(jy, jy, __fmul_rn(jx, jx))));
-    const float e0 = __fmul_rn((float)weight(0), __fsub_rn(drho, usq));
+    const float q = __fsub_rn(drho, usq);   // drho - 3/2 j.j: the isotropic part of e^+
+    const float e0 = __fmul_rn((float)weight(0), q);
     h[0] = fmaf(-c.omega_p, __fsub_rn(h[0], e0), h[0]);
+    const float qw[2] = {__fmul_rn((float)weight(1), q), __fmul_rn((float)weight(7), q)};
 #pragma unroll
     for (int k = 1; k < kQ; k += 2) {
-        const int kb = k + 1;
+        const int kb = k + 1, cls = k <= 6 ? 0 : 1;
         const float eu = e_dot(k, jx, jy, jz);
-        const float w = (float)weight(k);
-        const float ep = __fmul_rn(w, __fsub_rn(fmaf(__fmul_rn(c.eu_c, eu), eu, drho), usq));
-        const float em = __fmul_rn(3.0f * w, eu);
+        const float ep = fmaf(__fmul_rn(c.ep_c[cls], eu), eu, qw[cls]);
         const float dp = __fmul_rn(c.omega_p, fmaf(0.5f, __fadd_rn(h[k], h[kb]), -ep));
-        const float dm = __fmul_rn(c.omega_m, fmaf(0.5f, __fsub_rn(h[k], h[kb]), -em));
-        const float hk = __fadd_rn(__fsub_rn(__fsub_rn(h[k], dp), dm), c.force[k]);
-        const float hb = __fsub_rn(__fadd_rn(__fsub_rn(h[kb], dp), dm), c.force[k]);
+        const float dm = fmaf(c.half_omega_m, __fsub_rn(h[k], h[kb]), -fmaf(c.em_c[cls], eu, c.force[k]));
+        const float hk = __fsub_rn(__fsub_rn(h[k], dp), dm);
+        h[kb] = __fadd_rn(__fsub_rn(h[kb], dp), dm);
         h[k] = hk;
-        h[kb] = hb;
     }
 }
 
@@ -299,12 +306,19 @@ __device__ __forceinline__ void gather_odd(float h[kQ], const T *__restrict__ pd
     }
 }
 
-// Geometry of the row bitmasks (see lbm_internal.h).
+// Geometry of the row bitmasks of a single box (see lbm_internal.h).
 struct RowGeo {
     const uint2 *words;
     const uint32_t *cell_xr;
-    int nx, ny, nz, nw, x_bits, periodic_z;
+    int nx, ny, nz, nw, periodic_z;
 };
+
+__device__ __forceinline__ void unpack_xyz(uint32_t v, int &x, int &y, int &z)
+{
+    x = (int)(v & ((1u << kXyzBitsX) - 1u));
+    y = (int)((v >> kXyzBitsX) & ((1u << kXyzBitsY) - 1u));
+    z = (int)(v >> (kXyzBitsX + kXyzBitsY));
+}
 
 // Fluid index of bit b of a row word, -1 when the cell is solid.
 __device__ __forceinline__ int32_t word_pick(uint2 w, int b)
@@ -314,15 +328,44 @@ __device__ __forceinline__ int32_t word_pick(uint2 w, int b)
 }
 
 // Fluid indices of x-1, x, x+1 (periodic in x) in the row whose words start at
-// `row`: one word load, plus the neighbouring word at a word edge.
-__device__ __forceinline__ void row_triple(const RowGeo &g, const uint2 *row, int x, int xm, int xp, int32_t &im,
-                                           int32_t &i0, int32_t &ip)
+// `row` (global or shared memory): one word load, plus the neighbouring word
+// at a word edge.
+template <bool SHARED>
+__device__ __forceinline__ void row_triple(int nx, const uint2 *row, int x, int xm, int xp, int32_t &im, int32_t &i0,
+                                           int32_t &ip)
 {
+    auto load = [&](int w) { return SHARED ? row[w] : __ldg(row + w); };
     const int b = x & 31;
-    const uint2 c = __ldg(row + (x >> 5));
+    const uint2 c = load(x >> 5);
     i0 = word_pick(c, b);
-    im = b > 0 ? word_pick(c, b - 1) : word_pick(__ldg(row + (xm >> 5)), xm & 31);
-    ip = (b < 31 && x + 1 < g.nx) ? word_pick(c, b + 1) : word_pick(__ldg(row + (xp >> 5)), xp & 31);
+    im = b > 0 ? word_pick(c, b - 1) : word_pick(load(xm >> 5), xm & 31);
+    ip = (b < 31 && x + 1 < nx) ? word_pick(c, b + 1) : word_pick(load(xp >> 5), xp & 31);
+}
+
+// The 18 neighbours of a cell from the row words of its row (y, z) and the
+// rows (y +- 1, z +- 1); R(dy, dz) gives the words of row (y + dy, z + dz).
+// Writes nb[k] (-1: solid) and returns the link mask (bit k: x + e_k solid).
+template <bool SHARED, typename Rows>
+__device__ __forceinline__ uint32_t neighbours_from_rows(int32_t nb[kQ], Rows R, int nx, int x, int32_t i)
+{
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    int32_t self;
+    nb[0] = i;
+    row_triple<SHARED>(nx, R(0, 0), x, xm, xp, nb[2], self, nb[1]);      // -x, +x
+    row_triple<SHARED>(nx, R(1, 0), x, xm, xp, nb[10], nb[3], nb[7]);    // (-1,1,0) (0,1,0) (1,1,0)
+    row_triple<SHARED>(nx, R(-1, 0), x, xm, xp, nb[8], nb[4], nb[9]);    // (-1,-1,0) (0,-1,0) (1,-1,0)
+    row_triple<SHARED>(nx, R(0, 1), x, xm, xp, nb[14], nb[5], nb[11]);   // (-1,0,1) (0,0,1) (1,0,1)
+    row_triple<SHARED>(nx, R(0, -1), x, xm, xp, nb[12], nb[6], nb[13]);  // (-1,0,-1) (0,0,-1) (1,0,-1)
+    const int b = x & 31, w = x >> 5;
+    auto pick = [&](const uint2 *row) { return word_pick(SHARED ? row[w] : __ldg(row + w), b); };
+    nb[15] = pick(R(1, 1));     // (0,1,1)
+    nb[16] = pick(R(-1, -1));   // (0,-1,-1)
+    nb[17] = pick(R(1, -1));    // (0,1,-1)
+    nb[18] = pick(R(-1, 1));    // (0,-1,1)
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) m |= (uint32_t)(nb[k] < 0) << k;
+    return m;
 }
 
 // Neighbour indices of a fluid cell from the row bitmasks: the neighbour
@@ -332,11 +375,8 @@ __device__ __forceinline__ void row_triple(const RowGeo &g, const uint2 *row, in
 // never lie in a wall layer, so z +- 1 stays in the box when z is not periodic.
 __device__ __forceinline__ uint32_t row_neighbours(int32_t nb[kQ], const RowGeo &g, int32_t i)
 {
-    const uint32_t xr = g.cell_xr[i];
-    const int x = (int)(xr & ((1u << g.x_bits) - 1u));
-    const int row = (int)(xr >> g.x_bits);
-    const int y = row % g.ny, z = row / g.ny;
-    const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+    int x, y, z;
+    unpack_xyz(g.cell_xr[i], x, y, z);
     const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
     int zm = z - 1, zp = z + 1;
     if (g.periodic_z) {
@@ -344,23 +384,63 @@ __device__ __forceinline__ uint32_t row_neighbours(int32_t nb[kQ], const RowGeo 
         zp = zp >= g.nz ? zp - g.nz : zp;
     }
     const uint32_t nw = (uint32_t)g.nw, ny = (uint32_t)g.ny;
-    auto R = [&](int yy, int zz) { return g.words + ((uint32_t)yy + ny * (uint32_t)zz) * nw; };
-    int32_t self;
-    nb[0] = i;
-    row_triple(g, R(y, z), x, xm, xp, nb[2], self, nb[1]);       // -x, +x
-    row_triple(g, R(yp, z), x, xm, xp, nb[10], nb[3], nb[7]);    // (-1,1,0) (0,1,0) (1,1,0)
-    row_triple(g, R(ym, z), x, xm, xp, nb[8], nb[4], nb[9]);     // (-1,-1,0) (0,-1,0) (1,-1,0)
-    row_triple(g, R(y, zp), x, xm, xp, nb[14], nb[5], nb[11]);   // (-1,0,1) (0,0,1) (1,0,1)
-    row_triple(g, R(y, zm), x, xm, xp, nb[12], nb[6], nb[13]);   // (-1,0,-1) (0,0,-1) (1,0,-1)
-    const int b = x & 31, w = x >> 5;
-    nb[15] = word_pick(__ldg(R(yp, zp) + w), b);                 // (0,1,1)
-    nb[16] = word_pick(__ldg(R(ym, zm) + w), b);                 // (0,-1,-1)
-    nb[17] = word_pick(__ldg(R(yp, zm) + w), b);                 // (0,1,-1)
-    nb[18] = word_pick(__ldg(R(ym, zp) + w), b);                 // (0,-1,1)
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 1; k < kQ; ++k) m |= (uint32_t)(nb[k] < 0) << k;
-    return m;
+    auto R = [&](int dy, int dz) {
+        const int yy = dy < 0 ? ym : (dy > 0 ? yp : y), zz = dz < 0 ? zm : (dz > 0 ? zp : z);
+        return g.words + ((uint32_t)yy + ny * (uint32_t)zz) * nw;
+    };
+    return neighbours_from_rows<false>(nb, R, g.nx, x, i);
+}
+
+// A tile whose odd step stages row words in shared memory (Solver::tile_rows,
+// see k_stage_tiles): three bands (planes z - 1, z, z + 1) of band_rows rows
+// each, starting at row r0 (r = y + ny z) of the part whose words start at
+// words_base.
+struct StagedTile {
+    int32_t words_base, r0;
+    int band_rows, nw, periodic_z, nz, nx, ny;
+};
+
+__device__ __forceinline__ StagedTile staged_tile(int4 d)
+{
+    StagedTile t;
+    t.words_base = d.x;
+    t.r0 = d.y;
+    t.band_rows = d.z & 0xFF;
+    t.nw = (d.z >> 8) & 0x7F;
+    t.periodic_z = (d.z >> 15) & 1;
+    t.nz = d.z >> 16;
+    t.nx = d.w & 0xFFFF;
+    t.ny = d.w >> 16;
+    return t;
+}
+
+// Cooperative copy of the tile's bands into ws[3][band_rows][nw] (all
+// threads of the block); rows outside the part read as empty.
+__device__ __forceinline__ void stage_rows(uint2 *ws, const uint2 *__restrict__ words, const StagedTile &t)
+{
+    const int per_band = t.band_rows * t.nw, total = 3 * per_band, rows = t.ny * t.nz;
+    for (int e = threadIdx.x; e < total; e += kBlock) {
+        const int b = e / per_band, rem = e - b * per_band;
+        const int j = rem / t.nw, w = rem - j * t.nw;
+        const int row = t.r0 + (b - 1) * t.ny + j;
+        ws[e] = row >= 0 && row < rows ? __ldg(words + t.words_base + (int64_t)row * t.nw + w) : make_uint2(0u, 0u);
+    }
+}
+
+// Neighbour indices from the staged bands; false (nb untouched) when the cell
+// needs a row outside them: a neighbour row across the periodic wrap in y, or
+// in z for a periodic box.
+__device__ __forceinline__ bool staged_neighbours(int32_t nb[kQ], uint32_t &m, const uint2 *ws, int4 sd, uint32_t xyz,
+                                                  int32_t i)
+{
+    const StagedTile t = staged_tile(sd);
+    int x, y, z;
+    unpack_xyz(xyz, x, y, z);
+    if (y == 0 || y == t.ny - 1 || (t.periodic_z && (z == 0 || z == t.nz - 1))) return false;
+    const int lr = y + t.ny * z - t.r0;   // the cell's row within a band
+    auto R = [&](int dy, int dz) { return ws + ((dz + 1) * t.band_rows + lr + dy) * t.nw; };
+    m = neighbours_from_rows<true>(nb, R, t.nx, x, i);
+    return true;
 }
 
 // Neighbour indices of a cell of a dense tile (Solver::tile_desc d): the

@@ -33,7 +33,9 @@ constexpr int kOddBlocksPerSM = 6;
 // indices are computed.  Without dense tiles the table-only kernel is used:
 // it carries no descriptor load or branch (the periodic REV cubes, 2.7% faster
 // in the odd step).
-enum NbSource { kNbTable = 0, kNbRows = 1, kNbDense = 2 };
+// kNbStaged: the table's role outside the dense tiles is taken by row words
+// staged per tile in shared memory (LBM_FLAG_STAGED_NEIGHBOURS).
+enum NbSource { kNbTable = 0, kNbRows = 1, kNbDense = 2, kNbStaged = 3 };
 constexpr int kGridBulk = -1;       // schedule entry: the staged even step
 constexpr int kGraphSteps = 32;     // steps per CUDA-graph replay (even)
 constexpr int kTuneReps = 3;        // timed launches per candidate grid
@@ -46,6 +48,8 @@ struct StepArgs {
     const uint32_t *warp_off;
     const int2 *tile_desc;
     int32_t dense_lo, dense_hi;   // every dense tile lies in [dense_lo, dense_hi)
+    const int4 *tile_rows;
+    int32_t rows_lo, rows_hi;     // every staged tile lies in [rows_lo, rows_hi)
     const float *link_a;
     int *status;   // set to 1 when a bounded wait gives up
     int32_t n_fluid;
@@ -124,7 +128,7 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 // (the second read hits L1).
 // NB: where the neighbour indices come from (NbSource).
 template <typename T, int NB, bool REF>
-__device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock])
+__device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_t (*nb_s)[kBlock], uint2 *ws)
 {
     const int t = threadIdx.x;
     const bool live = i < p.n_fluid;
@@ -133,11 +137,23 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     uint32_t m = 0;
     // a dense tile (same for the whole block) computes its indices and has no links
     const int32_t tile = i / kBlock;
-    const int2 d = NB == kNbDense && tile >= p.dense_lo && tile < p.dense_hi ? __ldg(p.tile_desc + tile)
-                                                                            : make_int2(-1, 0);
+    const int2 d = (NB == kNbDense || NB == kNbStaged) && tile >= p.dense_lo && tile < p.dense_hi
+                       ? __ldg(p.tile_desc + tile)
+                       : make_int2(-1, 0);
+    // a staged tile (same for the whole block): its bands of row words go to
+    // shared memory once, after every thread is done with the previous tile's
+    const int4 sd = NB == kNbStaged && d.x < 0 && tile >= p.rows_lo && tile < p.rows_hi ? __ldg(p.tile_rows + tile)
+                                                                                       : make_int4(-1, 0, 0, 0);
+    if (NB == kNbStaged && sd.x >= 0) {
+        __syncthreads();
+        stage_rows(ws, p.rows.words, staged_tile(sd));
+        __syncthreads();
+    }
     if (live) {
         int32_t nb[kQ];
         if (d.x >= 0) dense_neighbours(nb, d, i);
+        else if (NB == kNbStaged && sd.x >= 0 && staged_neighbours(nb, m, ws, sd, __ldg(p.rows.cell_xr + i), i)) {
+        }
         else m = NB == kNbRows ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
         // stage the slot of direction k, A[k][x + e_k] or the dead slot
         // A[opp k][x] of a wall link: the gather of h_opp(k) reads it and the
@@ -287,8 +303,9 @@ template <typename T, int NB, int MINB, bool REF>
 __global__ void __launch_bounds__(kBlock, MINB) k_step_odd(StepArgs<T> p)
 {
     __shared__ int32_t nb_s[kQ - 1][kBlock];
+    __shared__ uint2 ws[NB == kNbStaged ? kMaxStagedWords : 1];
     for (int32_t tile = blockIdx.x; tile < p.n_tiles; tile += gridDim.x)
-        odd_cell<T, NB, REF>(p, tile * kBlock + threadIdx.x, nb_s);
+        odd_cell<T, NB, REF>(p, tile * kBlock + threadIdx.x, nb_s, ws);
 }
 
 // Initial state f_k = f_k^eq(rho = 1, u0) (Eq. (equilibrium)) stored shifted
@@ -344,7 +361,10 @@ StepArgs<T> make_args(const Solver &s)
     p.n_fluid = s.n_fluid;
     p.n_pad = s.n_pad;
     p.n_tiles = s.n_pad / kBlock;
-    p.rows = RowGeo{s.row_words, s.cell_xr, s.box.nx, s.box.ny, s.box.nz, s.n_words, s.x_bits, s.box.periodic_z};
+    p.rows = RowGeo{s.row_words, s.cell_xr, s.box.nx, s.box.ny, s.box.nz, s.n_words, s.box.periodic_z};
+    p.tile_rows = s.tile_rows;
+    p.rows_lo = s.rows_lo;
+    p.rows_hi = s.rows_hi;
     p.part_shift = s.part_shift;
     p.part_foff = s.part_foff;
     p.n_parts = (int32_t)s.parts.size();
@@ -361,6 +381,12 @@ StepArgs<T> make_args(const Solver &s)
     const float scale = StoreScale<T>::v;
     p.c.usq_c = 1.5f / scale;
     p.c.eu_c = 4.5f / scale;
+    p.c.half_omega_m = (float)(0.5 * s.omega_m);
+    for (int cls = 0; cls < 2; ++cls) {
+        const double w = cls == 0 ? weight(1) : weight(7);
+        p.c.ep_c[cls] = (float)(w * 4.5 / scale);
+        p.c.em_c[cls] = (float)(3.0 * w * s.omega_m);
+    }
     for (int k = 0; k < kQ; ++k) {
         const double eg = ex(k) * s.params.g[0] + ey(k) * s.params.g[1] + ez(k) * s.params.g[2];
         p.c.force[k] = (float)(3.0 * weight(k) * eg) * scale;
@@ -418,6 +444,8 @@ void launch_step_ref(const Solver &s, const StepArgs<T> &p, bool odd, int grid, 
     if (!odd && grid == kGridBulk) launch_even_bulk<T, EvenBulk<T>::S, EvenBulk<T>::MINB, REF>(p, st);
     else if (!odd) k_step_even<T, kEvenBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
     else if (s.odd_rows) k_step_odd<T, kNbRows, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
+    else if (s.staged_rows && p.rows_hi > p.rows_lo)
+        k_step_odd<T, kNbStaged, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
     else if (p.dense_hi > p.dense_lo) k_step_odd<T, kNbDense, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
     else k_step_odd<T, kNbTable, kOddBlocksPerSM, false><<<g, kBlock, 0, st>>>(p);
 }

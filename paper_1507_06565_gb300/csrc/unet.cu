@@ -822,6 +822,33 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
+// Weight gradient on the tensor cores: one CTA per (voxel chunk, tap) on grid
+// x; chunks of 128..4096 voxels (a power of two) so that the grid keeps ~16
+// CTAs per SM busy.  dw (fp32 [27][co][ci]) is accumulated into.
+static int launch_wgrad(const bf16 *dy, int co, const bf16 *in0, int ci0, const bf16 *in1, int ci1, float *dw,
+                        const Dims &g, cudaStream_t st, int *status)
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem) != cudaSuccess)
+            return LBM_ECUDA;
+        attr = true;
+    }
+    const int ci = ci0 + ci1;
+    const int64_t V = g.voxels();
+    if (co > kTcM || co % 16 != 0 || ci % 16 != 0 || ci > 256 || V >= ((int64_t)1 << 31)) return LBM_EINVAL;
+    int chunk = 4096;
+    while (chunk > 128 && (int64_t)kTaps * ((V + chunk - 1) / chunk) < 16 * 152) chunk >>= 1;
+    WgradArgs wa{dy, co, in0, ci0, in1, ci1, dw, g, chunk};
+    int ncols = 32;
+    while (ncols < ci) ncols <<= 1;
+    const size_t stage = (size_t)(co / 8 + ci / 8) * kWgSbo;
+    int stages = tc::kMaxStages;
+    while (stages > 2 && stages * stage + kWgTail > (size_t)kTcStepSmem) --stages;
+    k_wgrad_tc<<<(unsigned)(blocks(V, chunk) * kTaps), 128, stages * stage + kWgTail, st>>>(wa, ncols, stages, status);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
 static int conv(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1, int ci1, const Dims &g)
 {
     const Layer &L = net.layers[l];
@@ -837,31 +864,9 @@ static int conv_back(Net &net, int l, const bf16 *in0, int ci0, const bf16 *in1,
     Layer &L = net.layers[l];
     const int64_t V = g.voxels();
     k_relu_back<<<blocks(V * L.co), 256, 0, net.st>>>(net.dact[l], net.act[l], V * L.co);
-    // weight gradient on the tensor cores: one CTA per (voxel chunk, tap) on
-    // grid x; chunks of 128..4096 voxels (a power of two) so that the grid
-    // keeps ~16 CTAs per SM busy
     {
-        static bool attr = false;
-        if (!attr) {
-            if (cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem) !=
-                cudaSuccess)
-                return LBM_ECUDA;
-            attr = true;
-        }
-        const int ci = ci0 + ci1;
-        if (L.co > kTcM || L.co % 16 != 0 || ci % 16 != 0 || ci > 256 || V >= ((int64_t)1 << 31))
-            return LBM_EINVAL;
-        int chunk = 4096;
-        while (chunk > 128 && (int64_t)kTaps * ((V + chunk - 1) / chunk) < 16 * 152) chunk >>= 1;
-        WgradArgs wa{net.dact[l], L.co, in0, ci0, in1, ci1, net.grads + L.w_off, g, chunk};
-        int ncols = 32;
-        while (ncols < ci) ncols <<= 1;
-        const size_t stage = (size_t)(L.co / 8 + ci / 8) * kWgSbo;
-        int stages = tc::kMaxStages;
-        while (stages > 2 && stages * stage + kWgTail > (size_t)kTcStepSmem) --stages;
-        k_wgrad_tc<<<(unsigned)(blocks(V, chunk) * kTaps), 128, stages * stage + kWgTail, net.st>>>(wa, ncols, stages,
-                                                                                                    net.status);
-        if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+        const int rc = launch_wgrad(net.dact[l], L.co, in0, ci0, in1, ci1, net.grads + L.w_off, g, net.st, net.status);
+        if (rc != LBM_OK) return rc;
     }
     const int lanes = 256 / L.co;
     k_bias_grad<<<(unsigned)std::min<int64_t>(1024, blocks(V, lanes)), lanes * L.co, lanes * L.co * 4, net.st>>>(
@@ -1070,5 +1075,25 @@ int unet_adam_step(unet_net *net, float lr, float beta1, float beta2, float eps)
 }
 
 void unet_destroy(unet_net *net) { delete net; }
+
+int unet_conv3d(const uint16_t *dev_x, int32_t ci, const uint16_t *dev_w, const float *dev_bias, uint16_t *dev_y,
+                int32_t co, int32_t n, int32_t nz, int32_t ny, int32_t nx, int32_t relu, int32_t *dev_status,
+                void *stream)
+{
+    if (!dev_x || !dev_w || !dev_y || !dev_status || n < 1 || nz < 1 || ny < 1 || nx < 1) return LBM_EINVAL;
+    const Dims g{n, nz, ny, nx};
+    ConvArgs a{(const bf16 *)dev_x, ci, nullptr, 0, (const bf16 *)dev_w, dev_bias, (bf16 *)dev_y, co, nullptr, 0,
+               relu ? 1 : 0, g};
+    return launch_conv(a, (cudaStream_t)stream, dev_status);
+}
+
+int unet_conv3d_wgrad(const uint16_t *dev_dy, int32_t co, const uint16_t *dev_x, int32_t ci, float *dev_dw,
+                      int32_t n, int32_t nz, int32_t ny, int32_t nx, int32_t *dev_status, void *stream)
+{
+    if (!dev_dy || !dev_x || !dev_dw || !dev_status || n < 1 || nz < 1 || ny < 1 || nx < 1) return LBM_EINVAL;
+    const Dims g{n, nz, ny, nx};
+    return launch_wgrad((const bf16 *)dev_dy, co, (const bf16 *)dev_x, ci, nullptr, 0, dev_dw, g, (cudaStream_t)stream,
+                        dev_status);
+}
 
 }  // extern "C"

@@ -213,8 +213,8 @@ def test_recenter_keeps_velocity(torch_cuda):
 # storage precision bits: FP32 keeps the FP32 tolerance; FP16/BF16 use the
 # random-walk bound of their rounding, 10 (2^-p / 4) sqrt(n) 2 over n steps
 @pytest.mark.parametrize("storage,p_bits", [("f32", None), ("f16", 12), ("bf16", 9)])
-@pytest.mark.parametrize("flags", [0, L.LBM_FLAG_STAGED_EVEN, L.LBM_FLAG_ROW_NEIGHBOURS],
-                         ids=["plain", "staged-even", "row-neighbours"])
+@pytest.mark.parametrize("flags", [0, L.LBM_FLAG_STAGED_EVEN, L.LBM_FLAG_ROW_NEIGHBOURS, L.LBM_FLAG_STAGED_NEIGHBOURS],
+                         ids=["plain", "staged-even", "row-neighbours", "staged-neighbours"])
 def test_reference_populations_switch(torch_cuda, storage, p_bits, flags):
     """The free layer of the W1 channel stores its populations relative to
     the plane's reference equilibrium after a re-centring: the switch (one
@@ -224,16 +224,21 @@ def test_reference_populations_switch(torch_cuda, storage, p_bits, flags):
     tol = TOL_U if p_bits is None else 10 * 2.0 ** -p_bits / 4 * math.sqrt(184) * 2
     case = W.W1
     u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=3, amplitude=2e-2)
-    solver, lat, _ = _pair(torch_cuda, case, storage=storage, u0=u0, g=(3e-5, 0.0, 0.0), flags=flags)
+    solver, lat, _ = _pair(torch_cuda, case, storage=storage, u0=u0, g=(3e-5, 0.0, 0.0),
+                           flags=flags | L.LBM_FLAG_PLANE_REFERENCES)
     assert solver.reference_planes() > 20   # the free layer z = 32..62, less its edges
     fluid = solver.export_lists()["fluid_cell"]
+    shift = 0.0
     for n in (40, 41, 33):   # switches at even, odd and even parity
         solver.step(n)
         lat.step(n)
-        solver.recenter()
+        shift += solver.recenter()
     solver.step(70)
     lat.step(70)
-    got = solver.populations().cpu().numpy().astype(np.float64)
+    # the re-centring removed the mean density drift from every population
+    # (h_k - w_k c), which the oracle keeps: add it back before comparing
+    _, w = O.velocity_set()
+    got = solver.populations().cpu().numpy().astype(np.float64) + w[:, None] * shift
     want = _oracle_shifted(lat, fluid)
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
     _, u = solver.moments()
@@ -421,19 +426,21 @@ def test_one_cell_wide_column(torch_cuda, q):
         assert np.max(np.abs(got - want)) <= TOL_U * np.max(np.abs(want)), n
 
 
-@pytest.mark.parametrize("flags", [1, 2])
-def test_odd_step_variants_agree(torch_cuda, flags):
-    """Neighbour table and row-bitmask neighbours address the same slots, and
-    every rounding of the collision is explicit: the two kernels give the
-    same bits."""
-    case = CASES[2]
+@pytest.mark.parametrize("flags", [L.LBM_FLAG_ROW_NEIGHBOURS, L.LBM_FLAG_STAGED_NEIGHBOURS],
+                         ids=["row-neighbours", "staged-neighbours"])
+@pytest.mark.parametrize("case", [CASES[2], W.W1, CASES[1]], ids=lambda c: c.name)
+def test_odd_step_variants_agree(torch_cuda, flags, case):
+    """Neighbour table, row-bitmask neighbours and row words staged per tile
+    address the same slots, and every rounding of the collision is explicit:
+    the kernels give the same bits (periodic cube with wrap-around rows, the
+    W1 channel with dense tiles, a box whose planes hold fewer than a tile)."""
     u0 = W.velocity_field((case.nz, case.ny, case.nx), seed=5, amplitude=1e-2)
-    geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+    geom = L.lbm_geometry_from_spheres(*case.sphere_args(), q_lo=case.q_lo, q_hi=case.q_hi)
     import torch
 
     u0t = torch.from_numpy(u0).cuda()
     a = L.Solver(geom, u0=u0t, g=(1e-5, 0, 0), flags=flags)
-    b = L.Solver(geom, u0=u0t, g=(1e-5, 0, 0), flags=3 - flags)
+    b = L.Solver(geom, u0=u0t, g=(1e-5, 0, 0), flags=L.LBM_FLAG_NEIGHBOUR_TABLE)
     a.step(9)
     b.step(9)
     assert torch.equal(a.populations(), b.populations())
