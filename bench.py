@@ -298,6 +298,83 @@ def run_converge(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision_check(args):
+    """Converged error of FP16/BF16 storage (the reduced-precision
+    configuration): for each porosity, the channel in FP32 storage is run to
+    the profile tolerance from rest; FP16 and BF16 solvers then start from its
+    velocity field and run to the same tolerance.  Reports the permeability
+    and plane-profile differences of each against the FP32 result.  With
+    --oracle-steps N the FP64 oracle (host cores) continues the converged FP32
+    state for N steps and reports how far its profile moves, which bounds how
+    far the FP32 steady state lies from the oracle's."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+
+    build()
+    L.load_library()
+    phis = W.W2_POROSITIES if args.phi is None else [args.phi]
+    rows = []
+    for phi in phis:
+        c = W.W2(phi) if args.workload == "channel" else W.W2_half(phi)
+        geom = L.lbm_geometry_from_spheres(*c.sphere_args())
+        flags = odd_flags(args, [c])
+        out = {"case": c.name, "wall_rule": wall_rule(args, [c])}
+        s32 = L.Solver(geom, c.tau, c.lam, c.g, "f32", flags=flags)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, n, res = s32.run_until(args.tol, args.interval, args.max_steps, criterion="profile")
+        torch.cuda.synchronize()
+        out["f32"] = {"status": L.status_string(rc), "steps": n, "residual": res, "seconds": time.perf_counter() - t0,
+                      "permeability": s32.permeability(*c.perm_window)}
+        pa32 = s32.plane_average()[:, 0]
+        out["f32"]["u_sup_every8"] = pa32[::8].tolist()
+        _, u32 = s32.moments()
+        for st in ("f16", "bf16"):
+            s = L.Solver(geom, c.tau, c.lam, c.g, st, u0=u32, flags=flags)
+            t0 = time.perf_counter()
+            rc, n, res = s.run_until(args.tol, args.interval, args.max_steps, criterion="profile")
+            torch.cuda.synchronize()
+            k = s.permeability(*c.perm_window)
+            pa = s.plane_average()[:, 0]
+            out[st] = {"status": L.status_string(rc), "steps": n, "residual": res,
+                       "seconds": time.perf_counter() - t0, "permeability": k,
+                       "k_rel_vs_f32": k / out["f32"]["permeability"] - 1.0,
+                       "profile_l2_rel_vs_f32": float(np.linalg.norm(pa - pa32) / np.linalg.norm(pa32)),
+                       "profile_max_rel_vs_f32": float(np.max(np.abs(pa - pa32)) / np.max(np.abs(pa32)))}
+            del s
+        if args.oracle_steps > 0:
+            import oracle as O
+
+            lat = O.Lattice(c.nx, c.ny, c.nz, False, geom.spheres(), c.tau, c.lam, c.g,
+                            cli_safeguards=wall_rule(args, [c]) == "safeguards")
+            # the FP32 state as full populations f = h + w (lbm_populations
+            # gives h for every fluid cell)
+            h = s32.populations().cpu().numpy().astype(np.float64)
+            fluid = s32.export_lists()["fluid_cell"]
+            _, w = O.velocity_set()
+            f = np.zeros((19, c.nz * c.ny * c.nx))
+            f[:, fluid] = h + w[:, None]
+            lat.set_f(f)
+            p0 = lat.plane_average()[:, 0]
+            t0 = time.perf_counter()
+            lat.step(args.oracle_steps)
+            p1 = lat.plane_average()[:, 0]
+            out["oracle_continuation"] = {
+                "steps": args.oracle_steps, "seconds": time.perf_counter() - t0, "threads": O.threads(),
+                "profile_change_l2_rel": float(np.linalg.norm(p1 - p0) / np.linalg.norm(p1)),
+                "profile_vs_gpu_l2_rel": float(np.linalg.norm(p0 - pa32) / np.linalg.norm(pa32)),
+                "permeability_after": float(O.Lattice.permeability(lat, *c.perm_window))}
+        rows.append(out)
+        del s32
+        torch.cuda.empty_cache()
+    line = {"metric": f"converged FP16/BF16 error against FP32 (profile residual < {args.tol:g})", "unit": "relative",
+            "value": max(abs(r[st]["k_rel_vs_f32"]) for r in rows for st in ("f16", "bf16")), "higher_is_better": False,
+            "data": "synthetic", "config": {"workload": workload_name(args), "tol": args.tol}, "runs": rows}
+    print(json.dumps(line), flush=True)
+
+
 def unet_conv_flops(n, nz, ny, nx) -> float:
     """Multiply-adds x 2 of the 3x3x3 convolutions of one forward pass
     (27 taps x c_in x c_out per voxel of each layer's level)."""
@@ -911,6 +988,10 @@ def main():
                          "cli-stability: growth of a perturbation of the rest state on every packing")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
     ap.add_argument("--phi", type=float, default=None, help="--converge: one porosity of the channel sweep")
+    ap.add_argument("--precision-check", action="store_true",
+                    help="--converge: FP16/BF16 runs started from the converged FP32 field, errors against it")
+    ap.add_argument("--oracle-steps", type=int, default=0,
+                    help="--precision-check: FP64 oracle steps from the converged FP32 state")
     ap.add_argument("--converge", action="store_true",
                     help="instead of timing steps, run to steady state and report the time and permeabilities")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -939,6 +1020,8 @@ def main():
         run_re_sweep(args)
     elif args.workload == "cli-stability":
         run_cli_stability(args)
+    elif args.converge and args.precision_check:
+        run_precision_check(args)
     elif args.converge:
         run_converge(args)
     else:

@@ -337,6 +337,36 @@ __device__ __forceinline__ int32_t tap_nb(const Dims &g, int32_t v, int dz, int 
     return ((n * g.d + zz) * g.h + yy) * g.w + xx;
 }
 
+// Position of voxel v, decomposed once, for the tap neighbours of one voxel.
+struct VoxPos {
+    int32_t v;
+    int x, y, z;
+};
+
+__device__ __forceinline__ VoxPos vox_pos(const Dims &g, int32_t v)
+{
+    VoxPos p;
+    p.v = v;
+    p.x = v % g.w;
+    const int32_t r = v / g.w;
+    p.y = r % g.h;
+    p.z = (r / g.h) % g.d;
+    return p;
+}
+
+// tap_nb from a decomposed position: offsets and wrap corrections only
+__device__ __forceinline__ int32_t tap_nb(const Dims &g, const VoxPos &p, int dz, int dy, int dx)
+{
+    const int zz = p.z + dz;
+    if (zz < 0 || zz >= g.d) return -1;
+    const int32_t plane = g.h * g.w;
+    int32_t off = dz * plane + dy * g.w + dx;
+    const int yy = p.y + dy, xx = p.x + dx;
+    off += yy < 0 ? plane : (yy >= g.h ? -plane : 0);
+    off += xx < 0 ? g.w : (xx >= g.w ? -g.w : 0);
+    return p.v + off;
+}
+
 }  // namespace tc
 
 constexpr int kTcM = 128;
@@ -370,6 +400,7 @@ __global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, in
     const uint32_t tmem = tmem_slot;
     const int32_t v = m0 + tid;
     const bool vin = v < V;
+    const tc::VoxPos pos = tc::vox_pos(a.g, vin ? v : 0);
     const int chunks = ci / kc, iters = (kTaps / tp) * chunks;
     const uint32_t id = tc::idesc(kTcM, n, false);
     const uint32_t row_off = (uint32_t)(tid >> 3) * sbo + (uint32_t)(tid & 7) * 16u;
@@ -380,7 +411,7 @@ __global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, in
             const int t = tg * tp + q;
             const uint32_t sa = base + (uint32_t)s * stage_bytes + (uint32_t)q * a_bytes;
             const uint32_t sb = base + (uint32_t)s * stage_bytes + (uint32_t)tp * a_bytes + (uint32_t)q * b_bytes;
-            const int32_t nb = vin ? tc::tap_nb(a.g, v, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1) : -1;
+            const int32_t nb = vin ? tc::tap_nb(a.g, pos, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1) : -1;
             const bool valid = nb >= 0;
             for (int j = 0; j < kc / 8; ++j) {
                 const int c = c0 + 8 * j;
