@@ -237,6 +237,11 @@ def odd_flags(args, cases=()) -> int:
         flags |= L.LBM_FLAG_SIMPLE_BOUNCE_BACK
     if getattr(args, "even", "auto") == "staged":
         flags |= L.LBM_FLAG_STAGED_EVEN
+    refs = getattr(args, "plane_references", "auto")
+    if refs == "on":
+        flags |= L.LBM_FLAG_PLANE_REFERENCES
+    elif refs == "off":
+        flags |= L.LBM_FLAG_NO_PLANE_REFERENCES
     if wall_rule(args, cases) == "safeguards":
         flags |= L.LBM_FLAG_CLI_SAFEGUARDS
     return flags
@@ -320,7 +325,7 @@ def run_precision_check(args):
         c = W.W2(phi) if args.workload == "channel" else W.W2_half(phi)
         geom = L.lbm_geometry_from_spheres(*c.sphere_args())
         flags = odd_flags(args, [c])
-        out = {"case": c.name, "wall_rule": wall_rule(args, [c])}
+        out = {"case": c.name, "wall_rule": wall_rule(args, [c]), "plane_references": args.plane_references}
         s32 = L.Solver(geom, c.tau, c.lam, c.g, "f32", flags=flags)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -334,7 +339,7 @@ def run_precision_check(args):
         for st in ("f16", "bf16"):
             s = L.Solver(geom, c.tau, c.lam, c.g, st, u0=u32, flags=flags)
             t0 = time.perf_counter()
-            rc, n, res = s.run_until(args.tol, args.interval, args.max_steps, criterion="profile")
+            rc, n, res = s.run_until(args.tol, args.interval, args.rp_max_steps, criterion="profile")
             torch.cuda.synchronize()
             k = s.permeability(*c.perm_window)
             pa = s.plane_average()[:, 0]
@@ -434,6 +439,76 @@ def run_unet(args):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_kind": kind,
                          "flops": "3 x forward convolution FLOPs (forward, input and weight gradients) per step"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_unet_layers(args):
+    """Per-layer throughput of the U-Net's tensor-core contractions (the
+    training shape: batch 4 of 64x64x128 fields): every 3x3x3 layer's forward
+    convolution, its input gradient (the same kernel with the transposed
+    weights) and its weight gradient, each timed alone with CUDA events over
+    --steps launches, as TFLOP/s against the bf16 peak and as GB/s of the
+    activations it must read and write once."""
+    import torch
+
+    import paper_1507_06565_gb300 as L
+    from paper_1507_06565_gb300.build import build
+    from paper_1507_06565_gb300.workloads import UNET_LAYERS
+
+    build()
+    L.load_library()
+    n, nz, ny, nx = 4, 128, 64, 64
+    level = {"enc1": 0, "enc2": 1, "enc3": 2, "bott": 3, "dec3": 2, "dec2": 1, "dec1": 0}
+    try:
+        with open(PEAKS_FILE) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        peak, kind = 1900.0, "fallback"
+    hbm, _ = _peak_hbm()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for name, co, ci in UNET_LAYERS:
+        lv = level[name[:4]]
+        dims = (n, nz >> lv, ny >> lv, nx >> lv)
+        V = int(np.prod(dims))
+        x = (torch.rand((V, ci), device="cuda", generator=gen) - 0.5).to(torch.bfloat16)
+        dy = (torch.rand((V, co), device="cuda", generator=gen) - 0.5).to(torch.bfloat16)
+        w = ((torch.rand((27, co, ci), device="cuda", generator=gen) - 0.5) * 0.1).to(torch.bfloat16)
+        wt = w.flip(0).transpose(1, 2).contiguous()   # the input gradient's weights
+        b = torch.zeros(co, device="cuda")
+        y = torch.empty((V, co), dtype=torch.bfloat16, device="cuda")
+        dx = torch.empty((V, ci), dtype=torch.bfloat16, device="cuda")
+        dw = torch.zeros((27, co, ci), device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        flops = 2.0 * 27 * co * ci * V
+        rec = {"layer": name, "level": lv, "c_in": ci, "c_out": co, "voxels": V, "gflop": flops / 1e9}
+        for kind_, fn, io in (
+                ("forward", lambda: L.unet_conv3d(x, w, b, co, dims, True, out=y, status=status), V * (ci + co) * 2),
+                ("input_grad", lambda: L.unet_conv3d(dy, wt, None, ci, dims, False, out=dx, status=status),
+                 V * (ci + co) * 2),
+                ("weight_grad", lambda: L.unet_conv3d_wgrad(dy, x, dims, dw=dw, status=status), V * (ci + co) * 2)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            tf = flops / (ms * 1e-3) / 1e12
+            rec[kind_] = {"ms": ms, "tflops": tf, "frac_bf16": tf / peak, "gbs_io": io / (ms * 1e-3) / 1e9,
+                          "frac_hbm_io": io / (ms * 1e-3) / 1e9 / hbm}
+        assert int(status.item()) == 0, "a tensor-core wait gave up"
+        rows.append(rec)
+    tot_ms = sum(r[k]["ms"] for r in rows for k in ("forward", "input_grad", "weight_grad"))
+    tot_fl = sum(3 * r["gflop"] for r in rows) * 1e9
+    line = {"metric": "U-Net layer contractions (forward, input gradient, weight gradient)", "unit": "TFLOP/s",
+            "value": tot_fl / (tot_ms * 1e-3) / 1e12, "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic", "peak": peak, "peak_kind": kind, "steps": args.steps,
+            "config": {"workload": f"batch {n} of {nz}x{ny}x{nx} fields, the 14 3x3x3 layers"}, "layers": rows}
     print(json.dumps(line), flush=True)
 
 
@@ -978,7 +1053,7 @@ def main():
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (FP32 collision in every case)")
     ap.add_argument("--workload", choices=["channel", "channel-half", "large", "w0", "rev", "surrogate", "unet", "glbm",
-                                           "homogenised", "grid-study", "re-sweep", "cli-stability"],
+                                           "homogenised", "grid-study", "re-sweep", "cli-stability", "unet-layers"],
                     default="channel",
                     help="channel: the 256x256x512 sweep (the benchmark); channel-half: 128x128x256, for "
                          "profiling; large: one 512x512x1024 channel; rev: the batched REV cubes; surrogate: "
@@ -990,6 +1065,11 @@ def main():
     ap.add_argument("--phi", type=float, default=None, help="--converge: one porosity of the channel sweep")
     ap.add_argument("--precision-check", action="store_true",
                     help="--converge: FP16/BF16 runs started from the converged FP32 field, errors against it")
+    ap.add_argument("--rp-max-steps", type=int, default=400_000,
+                    help="--precision-check: step limit of the FP16/BF16 runs (their profile residual floor can "
+                         "lie above --tol)")
+    ap.add_argument("--plane-references", choices=["auto", "on", "off"], default="auto",
+                    help="plane reference equilibria: the library default (on for FP16/BF16 storage), or forced")
     ap.add_argument("--oracle-steps", type=int, default=0,
                     help="--precision-check: FP64 oracle steps from the converged FP32 state")
     ap.add_argument("--converge", action="store_true",
@@ -1012,6 +1092,8 @@ def main():
         run_unet(args)
     elif args.workload == "glbm":
         run_glbm(args)
+    elif args.workload == "unet-layers":
+        run_unet_layers(args)
     elif args.workload == "homogenised":
         run_homogenised(args)
     elif args.workload == "grid-study":

@@ -144,12 +144,17 @@ typedef struct {
  * fully fluid planes whose neighbour planes are fully fluid store each
  * population relative to the equilibrium of the plane's mean velocity, which
  * lbm_recenter refreshes.  Storage rounding then acts on the small
- * non-equilibrium part only: in FP16/BF16 storage the free-channel velocity
- * error falls by about an order of magnitude.  It costs the step kernels one
- * reference load and one addition per population in those planes (measured
- * 3% of the FP32 and 7% of the FP16 step on the 256x256x512 channels), so it
- * is off by default. */
+ * non-equilibrium part only.  In FP16/BF16 storage, where that rounding
+ * dominates, it cuts the steady-channel velocity error by two orders of
+ * magnitude (measured: FP16 11% -> 0.03%, BF16 59% -> 0.4% of u_max on a
+ * 16x16x34 channel) and is on by default; LBM_FLAG_NO_PLANE_REFERENCES turns
+ * it off.  In FP32 storage the collision's own roundings dominate, so it is
+ * off unless LBM_FLAG_PLANE_REFERENCES asks for it.  It costs the step
+ * kernels one reference load and one addition per population in those
+ * planes (measured 3% of the FP32 and 7% of the FP16 step on the
+ * 256x256x512 channels). */
 #define LBM_FLAG_PLANE_REFERENCES 512
+#define LBM_FLAG_NO_PLANE_REFERENCES 1024
 
 /* Flow parameters.  tau = 1/omega+ with 1/omega+ = 3 nu + 1/2 (Sec. 2.1);
  * lambda is the magic parameter (1/omega+ - 1/2)(1/omega- - 1/2), which fixes
@@ -311,7 +316,8 @@ int lbm_mass(lbm_solver *solver, double *mean_drho);
  * Eq. (CLI), a w - a w + w = w, all commute with it), so velocities are
  * unchanged in exact arithmetic; it keeps the stored populations small so
  * that reduced-precision storage keeps its resolution in long runs.
- * With LBM_FLAG_PLANE_REFERENCES it also refreshes the reference populations
+ * With plane references (the FP16/BF16 default, LBM_FLAG_PLANE_REFERENCES
+ * for FP32) it also refreshes the reference populations
  * of the solver's translation-invariant planes (fully fluid planes whose
  * neighbour planes are fully fluid too, e.g. the free channel above a porous
  * layer): there every slot stores its population minus the equilibrium
@@ -352,8 +358,8 @@ int lbm_load(lbm_solver *solver, const void *host_buf, size_t bytes);
 /* Number of planes (over all parts) whose slots store populations relative
  * to the plane's reference equilibrium (LBM_FLAG_PLANE_REFERENCES, see
  * lbm_recenter): fully fluid planes whose neighbour planes are fully fluid
- * and lie in tiles of 256 cells that hold only such planes' cells; 0 without
- * the flag. */
+ * and lie in tiles of 256 cells that hold only such planes' cells; 0 when
+ * plane references are off. */
 int lbm_reference_planes(const lbm_solver *solver, int32_t *n_planes);
 
 /* Steps taken since lbm_init/lbm_reset. */

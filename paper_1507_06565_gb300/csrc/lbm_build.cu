@@ -508,7 +508,7 @@ int device_build(Solver &s, const std::vector<const Geometry *> &geoms)
         // reference planes and the tiles that use them (see lbm_internal.h)
         std::vector<int2> tref(desc.size(), make_int2(-1, 0));
         s.plane_referenced.assign((size_t)s.lay.n_planes, 0);
-        if (s.params.flags & LBM_FLAG_PLANE_REFERENCES) mark_reference_planes(s, desc, poff, tref);
+        if (plane_references_on(s.params)) mark_reference_planes(s, desc, poff, tref);
         s.ref_lo = s.ref_hi = 0;
         for (size_t t = 0; t < tref.size(); ++t)
             if (tref[t].x >= 0) {

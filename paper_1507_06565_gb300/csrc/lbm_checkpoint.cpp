@@ -64,7 +64,8 @@ Header header_of(const Solver &s)
     std::memcpy(h.magic, kMagic, 8);
     h.version = kVersion;
     h.storage = s.params.storage;
-    h.flags = s.params.flags & kStateFlags;
+    h.flags = (s.params.flags & kStateFlags & ~LBM_FLAG_PLANE_REFERENCES) |
+              (plane_references_on(s.params) ? LBM_FLAG_PLANE_REFERENCES : 0);
     h.n_parts = (int32_t)s.parts.size();
     h.n_cells = s.n_cells;
     h.n_fluid = s.n_fluid;

@@ -269,6 +269,13 @@ int launch_populations(Solver &s, float *out);
 int launch_reference_update(Solver &s);                    // u_cur -> ref_next
 
 // ---- shared host helpers ----
+// plane reference equilibria in use: FP16/BF16 storage unless turned off,
+// FP32 storage when asked for
+inline bool plane_references_on(const lbm_params &p)
+{
+    if (p.flags & LBM_FLAG_PLANE_REFERENCES) return true;
+    return p.storage != LBM_F32 && !(p.flags & LBM_FLAG_NO_PLANE_REFERENCES);
+}
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 inline int storage_bytes(int storage) { return storage == LBM_F32 ? 4 : 2; }
 

@@ -137,9 +137,9 @@ def _fp32_channel_bias(H, nu):
     return 2.0 ** -24 * H * H / (8.0 * nu)
 
 
-def _steady_channel(nx, nz, tau, lam, q_lo, q_hi, g, flags=0):
+def _steady_channel(nx, nz, tau, lam, q_lo, q_hi, g, flags=0, storage="f32"):
     geom = L.lbm_geometry_from_list(nx, nx, nz, False, [], q_lo=q_lo, q_hi=q_hi)
-    solver = L.Solver(geom, tau, lam, (g, 0.0, 0.0), flags=flags)
+    solver = L.Solver(geom, tau, lam, (g, 0.0, 0.0), storage, flags=flags)
     nu = (tau - 0.5) / 3
     H = nz - 2
     nsteps = int(40 * H * H / (math.pi ** 2 * nu)) + 201
@@ -172,15 +172,21 @@ def test_channel_closed_form_on_gpu(torch_cuda, tau, lam, q_lo, q_hi):
     assert np.max(np.abs(ux - exact)) <= tol * np.max(exact)
 
 
-def test_plane_references_remove_the_channel_bias(torch_cuda):
-    """With reference equilibria in the planes away from the walls, the FP32
-    bias of the steady channel falls well below the plain storage's."""
-    nz, g, tau, lam = 18, 1e-6, 0.8, 3 / 16
-    ux, exact = _steady_channel(16, nz, tau, lam, 0.5, 0.5, g)
-    ux_r, _ = _steady_channel(16, nz, tau, lam, 0.5, 0.5, g, flags=L.LBM_FLAG_PLANE_REFERENCES)
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_plane_references_cut_the_reduced_precision_bias(torch_cuda, storage):
+    """In FP16/BF16 storage the rounding of the stored populations dominates
+    the error of a steady channel (the collision rounds in FP32); with the
+    plane reference equilibria the stored values are the small
+    non-equilibrium parts, and the error against the closed form falls by at
+    least half.  (In FP32 storage the collision's own roundings at the full
+    magnitude dominate, so the references do not help there: measured 1.8e-5
+    plain, 2.2e-5 with references.)"""
+    nz, g, tau, lam = 34, 1e-6, 0.8, 3 / 16
+    ux, exact = _steady_channel(16, nz, tau, lam, 0.5, 0.5, g, storage=storage, flags=L.LBM_FLAG_NO_PLANE_REFERENCES)
+    ux_r, _ = _steady_channel(16, nz, tau, lam, 0.5, 0.5, g, storage=storage)   # references: the 16-bit default
     e, e_r = (np.max(np.abs(v - exact)) / np.max(exact) for v in (ux, ux_r))
-    print(f"\nchannel bias: plain {e:.2e}, with plane references {e_r:.2e}")
-    assert e_r <= TOL_U and e_r < 0.5 * e
+    print(f"\n{storage} channel error: plain {e:.2e}, with plane references {e_r:.2e}")
+    assert e_r < 0.5 * e
 
 
 def test_permeability_converged(torch_cuda):

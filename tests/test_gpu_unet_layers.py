@@ -29,6 +29,9 @@ def torch_cuda():
 
 
 DIMS = (2, 6, 10, 12)   # n, nz, ny, nx: 1440 voxels, a ragged last tile of 128
+# boxes whose x-rows of 32 / 64 voxels take the halo-tile kernel (128 voxels =
+# 4 / 2 rows of one plane), with wrap-around in y and zeros beyond z
+HALO_DIMS = [(2, 3, 4, 32), (1, 4, 2, 64), (1, 2, 8, 64)]
 
 
 def _bf16_tensor(torch, a):
@@ -40,15 +43,16 @@ def _per_sample(a):
     return [np.moveaxis(a[s], -1, 0) for s in range(a.shape[0])]
 
 
-@pytest.mark.parametrize("ci,co", [(16, 16), (48, 16), (32, 64), (64, 128), (192, 64), (96, 32)])
-def test_conv3d_forward_elementwise(torch_cuda, ci, co):
+@pytest.mark.parametrize("dims", [DIMS] + HALO_DIMS, ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("ci,co", [(16, 16), (48, 16), (32, 64), (64, 128), (192, 64), (96, 32), (32, 96)])
+def test_conv3d_forward_elementwise(torch_cuda, ci, co, dims):
     torch = torch_cuda
     rng = np.random.default_rng(ci * 1000 + co)
-    x = U.bf16(rng.standard_normal(DIMS + (ci,)))
+    x = U.bf16(rng.standard_normal(dims + (ci,)))
     w = U.bf16(rng.standard_normal((27, co, ci)) / np.sqrt(27 * ci))
     b = rng.standard_normal(co).astype(np.float32).astype(np.float64)
     y = L.unet_conv3d(_bf16_tensor(torch, x), _bf16_tensor(torch, w), torch.from_numpy(b.astype(np.float32)).cuda(),
-                      co, DIMS, relu=True).float().cpu().numpy().astype(np.float64)
+                      co, dims, relu=True).float().cpu().numpy().astype(np.float64)
     for s, xs in enumerate(_per_sample(x)):
         exact = np.maximum(U.conv3(xs, w, b), 0.0)
         absum = U.conv3(np.abs(xs), np.abs(w), np.abs(b))
