@@ -723,10 +723,10 @@ def run_surrogate(args):
 
     build()
     L.load_library()
-    shape = (64, 64, 128)
+    shape = tuple(int(v) for v in args.shape.split("x"))
     t0 = time.perf_counter()
-    data = S.generate(range(500000, 500000 + args.train_samples), shape, tol=1e-6)
-    tr = S.train(data, epochs=args.epochs, lr=2e-3, batch=4)
+    data = S.generate(range(500000, 500000 + args.train_samples), shape, tol=args.label_tol)
+    tr = S.train(data, epochs=args.epochs, lr=2e-3, batch=args.batch)
     params = tr.net.params().cpu().numpy()
     rows = S.warm_vs_cold(params, range(600000, 600000 + args.heldout), shape, tol=args.tol)
     cold = sum(r["cold"]["seconds"] for r in rows)
@@ -738,7 +738,8 @@ def run_surrogate(args):
             "dtype": "f32 LBM, bf16/fp32 network", "data": "synthetic",
             "config": {"workload": f"{shape[0]}x{shape[1]}x{shape[2]} channels, lower half overlapping r=4 spheres at "
                                    "porosity U[0.6,0.8]; train seeds 500000+, held-out seeds 600000+",
-                       "train_samples": args.train_samples, "heldout": args.heldout, "epochs": args.epochs},
+                       "train_samples": args.train_samples, "heldout": args.heldout, "epochs": args.epochs,
+                       "batch": args.batch, "label_tol": args.label_tol, "wall_rule": "safeguards"},
             "training": {"data_steps": data.steps, "data_s": data.seconds, "train_s": tr.seconds,
                          "samples": tr.samples, "loss_first": tr.losses[0], "loss_last": float(np.mean(tr.losses[-8:]))},
             "rows": rows, "total_s": time.perf_counter() - t0}
@@ -976,20 +977,25 @@ def run_ours(args, world, rank, local):
                                                    + MEASURED_DRAM_B_PER_FLUP_REV["odd"])
 
     # end to end through the public API with host buffers: lbm_init from the
-    # host geometry (mask and sphere bins copied host->device), E2E_STEPS
-    # steps, plane averages copied back to the host
-    e2e_steps = max(10, args.steps // 4)
+    # host geometry (mask and sphere bins copied host->device, lists and
+    # links built on the device), the steps through lbm_step (the schedule
+    # tuner's trial launches included), plane averages copied back to the
+    # host; at least 200 steps so that the set-up is amortised as in a run
+    e2e_steps = max(200, args.steps)
     torch.cuda.synchronize()
     te = time.perf_counter()
     h2d = 0
     d2h = 0
+    setup_s = 0.0
     groups = [geoms] if args.workload == "rev" else [[g] for g in geoms]
     grp_case = {id(g): c for g, c in zip(geoms, cases)}
     for grp in groups:
+        t_in = time.perf_counter()
         if args.workload == "rev":
             s2 = L.BatchSolver(grp, c0.tau, c0.lam, c0.g, args.storage, flags=odd_flags(args, cases))
         else:
             s2 = L.Solver(grp[0], c0.tau, c0.lam, c0.g, args.storage, flags=odd_flags(args, [grp_case[id(grp[0])]]))
+        setup_s += time.perf_counter() - t_in
         s2.step(e2e_steps)
         pa = s2.plane_average()
         h2d += sum(g.mask().nbytes for g in grp)
@@ -1017,8 +1023,9 @@ def run_ours(args, world, rank, local):
                      "bytes_per_flup": bytes_per_flup, "peak_kind": peak_kind, "by_kernel": parity,
                      "wall_frac": value * 1e6 / world * bytes_per_flup / 1e9 / peak},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / e2e_steps,
-                "d2h_bytes_per_step": d2h / e2e_steps,
-                "what": f"lbm_init from host geometry + {e2e_steps} steps + plane averages to host, all four solvers"},
+                "d2h_bytes_per_step": d2h / e2e_steps, "steps": e2e_steps, "seconds": e2e_s,
+                "setup_seconds": setup_s,
+                "what": f"lbm_init from host geometry + {e2e_steps} steps + plane averages to host, every solver"},
         "clocks": clk,
         "gpu_launches": args.steps * len(solvers),
     }
@@ -1078,6 +1085,9 @@ def main():
     ap.add_argument("--train-samples", type=int, default=96)
     ap.add_argument("--heldout", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--shape", default="64x64x128", help="surrogate: channel nx x ny x nz")
+    ap.add_argument("--batch", type=int, default=4, help="surrogate: training batch")
+    ap.add_argument("--label-tol", type=float, default=1e-6, help="surrogate: profile residual of the labels")
     ap.add_argument("--interval", type=int, default=500)
     ap.add_argument("--max-steps", type=int, default=2_000_000)
     args = ap.parse_args()

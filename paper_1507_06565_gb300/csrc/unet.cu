@@ -706,6 +706,107 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(WgradArgs a, int ncols, int st
     tc::teardown(tmem, ncols);
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient with the taps stacked along M.  By the adjoint shift,
+// dW[t][o][c] = sum_u dY[u - off_t][o] X[u][c]; with rows (t, o) one M = 128
+// tile holds T = 128 / co taps, so no accumulator row is wasted (co = 16 in a
+// plain dY^T X_t tile would use 16 of its 128 rows), X rows (B, N = ci, MN-major)
+// are plain copies shared by every tap, and only dY is gathered, shifted by
+// -off_t (circular in x and y, zero beyond z).  A CTA owns a chunk of voxels
+// (grid x) and G consecutive tiles (grid y, G ci <= 512 TMEM columns, one
+// accumulator of ci columns per tile); K runs over the chunk in steps of
+// kWsStep voxels through the barrier-free pipeline, and the epilogue adds each
+// tile's rows to dW[t][o][.] with fp32 atomics.
+// ---------------------------------------------------------------------------
+struct WstackArgs {
+    const bf16 *dy;
+    int co;
+    const bf16 *x0;
+    int ci0;
+    const bf16 *x1;
+    int ci1;    // the input is [x0, x1] (x1: ci1 = 0 for none)
+    float *dw;   // [27][co][ci] fp32 (accumulated)
+    Dims g;
+    int chunk;   // voxels per CTA (a multiple of kWsStep)
+    int tiles;   // tiles per CTA
+};
+
+constexpr int kWsStep = 32;
+constexpr uint32_t kWsSbo = kWsStep * 16;                  // bytes per 8-element MN group
+constexpr uint32_t kWsTileBytes = (kTcM / 8) * kWsSbo;      // one A tile (128 rows)
+
+__global__ void __launch_bounds__(128) k_wgrad_stack(WstackArgs a, int ncols, int stages, int *status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[tc::kMaxStages], empty[tc::kMaxStages];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int co = a.co, ci = a.ci0 + a.ci1, T = kTcM / co;
+    const int n_tiles = (kTaps + T - 1) / T;
+    const int tile0 = (int)blockIdx.y * a.tiles;
+    const int G = min(a.tiles, n_tiles - tile0);
+    const int32_t V = (int32_t)a.g.voxels();
+    const int32_t v_begin = (int32_t)blockIdx.x * a.chunk;
+    const uint32_t b_bytes = (uint32_t)(ci / 8) * kWsSbo;
+    const uint32_t stage_bytes = (uint32_t)a.tiles * kWsTileBytes + b_bytes;
+    const uint32_t base = tc::smem_u32(smem);
+    tc::setup(&tmem_slot, full, empty, stages, ncols);
+    const uint32_t tmem = tmem_slot;
+    const uint32_t id = tc::idesc(kTcM, ci, true);
+    const int iters = a.chunk / kWsStep;
+    const int k = tid % kWsStep, part = tid / kWsStep;   // the step's voxel k; 4 parts share its pieces
+    const uint32_t k_off = (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 16u;
+    const int pieces_o = co / 8;
+
+    auto fill = [&](int it, int s) {
+        const uint32_t st0 = base + (uint32_t)s * stage_bytes, sb = st0 + (uint32_t)a.tiles * kWsTileBytes;
+        const int32_t u = v_begin + it * kWsStep + k;
+        const bool uin = u < V;
+        const tc::VoxPos pos = tc::vox_pos(a.g, uin ? u : 0);
+        for (int q = part; q < ci / 8; q += 4) {
+            const int c = 8 * q;
+            const bf16 *src = c < a.ci0 ? a.x0 + (int64_t)u * a.ci0 + c : a.x1 + (int64_t)u * a.ci1 + (c - a.ci0);
+            tc::cp16(sb + (uint32_t)q * kWsSbo + k_off, uin ? (const void *)src : (const void *)a.x0, uin);
+        }
+        for (int j = 0; j < G; ++j) {
+            const uint32_t sa = st0 + (uint32_t)j * kWsTileBytes;
+            for (int e = part; e < 16; e += 4) {   // T taps x co/8 pieces = 16 MN groups
+                const int tl = e / pieces_o, p = e % pieces_o;
+                const int t = (tile0 + j) * T + tl;
+                int32_t nb = -1;
+                if (uin && t < kTaps) nb = tc::tap_nb(a.g, pos, 1 - t / 9, 1 - (t / 3) % 3, 1 - t % 3);
+                const bool valid = nb >= 0;
+                tc::cp16(sa + (uint32_t)e * kWsSbo + k_off,
+                         valid ? (const void *)(a.dy + (int64_t)nb * co + 8 * p) : (const void *)a.dy, valid);
+            }
+        }
+    };
+    auto issue = [&](int it, int s) {
+        const uint32_t st0 = base + (uint32_t)s * stage_bytes, sb = st0 + (uint32_t)a.tiles * kWsTileBytes;
+        for (int j = 0; j < G; ++j)
+            for (int jj = 0; jj < kWsStep / 16; ++jj)
+                tc::mma(tmem + (uint32_t)(j * ci), tc::desc(st0 + (uint32_t)j * kWsTileBytes + (uint32_t)jj * 256u, 128u, kWsSbo),
+                        tc::desc(sb + (uint32_t)jj * 256u, 128u, kWsSbo), id, it > 0 || jj > 0);
+    };
+    const bool ok = tc::pipeline(iters, stages, full, empty, status, fill, issue);
+    if (ok) {
+        const int row = warp * 32 + lane, tl = row / co, o = row % co;
+        for (int j = 0; j < G; ++j) {
+            const int t = (tile0 + j) * T + tl;
+            for (int c0 = 0; c0 < ci; c0 += 16) {
+                uint32_t r[16];
+                tc::load16(tmem, warp, j * ci + c0, r);
+                if (t < kTaps) {
+                    float *dst = a.dw + ((int64_t)t * co + o) * ci + c0;
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) atomicAdd(dst + jj, __uint_as_float(r[jj]));
+                }
+            }
+        }
+    }
+    tc::teardown(tmem, ncols);
+}
+
 // bias gradient: db[o] += sum_v dY[v][o]
 __global__ void k_bias_grad(const bf16 *__restrict__ dy, int co, int64_t V, float *__restrict__ db)
 {
@@ -1040,6 +1141,31 @@ static int launch_wgrad(const bf16 *dy, int co, const bf16 *in0, int ci0, const 
     const int ci = ci0 + ci1;
     const int64_t V = g.voxels();
     if (co > kTcM || co % 16 != 0 || ci % 16 != 0 || ci > 256 || V >= ((int64_t)1 << 31)) return LBM_EINVAL;
+    if (kTcM % co == 0) {
+        // taps stacked along M
+        static bool sattr = false;
+        if (!sattr) {
+            if (cudaFuncSetAttribute(k_wgrad_stack, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem) !=
+                cudaSuccess)
+                return LBM_ECUDA;
+            sattr = true;
+        }
+        const int T = kTcM / co, n_tiles = (kTaps + T - 1) / T;
+        int tiles = std::min(n_tiles, std::min(4, 512 / ci));
+        const int groups = (n_tiles + tiles - 1) / tiles;
+        tiles = (n_tiles + groups - 1) / groups;   // even split over the groups
+        int ncols = 32;
+        while (ncols < tiles * ci) ncols <<= 1;
+        int chunk = 4096;
+        while (chunk > 256 && ((V + chunk - 1) / chunk) * groups < 4 * 152) chunk >>= 1;
+        const size_t stage = (size_t)tiles * kWsTileBytes + (size_t)(ci / 8) * kWsSbo;
+        int stages = 3;
+        while (stages > 2 && stages * stage > (size_t)kTcMaxSmem) --stages;
+        WstackArgs wa{dy, co, in0, ci0, in1, ci1, dw, g, chunk, tiles};
+        const dim3 grid((unsigned)((V + chunk - 1) / chunk), (unsigned)groups);
+        k_wgrad_stack<<<grid, 128, stages * stage, st>>>(wa, ncols, stages, status);
+        return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    }
     int chunk = 4096;
     while (chunk > 128 && (int64_t)kTaps * ((V + chunk - 1) / chunk) < 16 * 152) chunk >>= 1;
     WgradArgs wa{dy, co, in0, ci0, in1, ci1, dw, g, chunk};
