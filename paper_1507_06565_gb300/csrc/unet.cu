@@ -471,15 +471,16 @@ __global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, in
 // are 32 or 64 voxels (the full- and half-resolution levels, which carry most
 // of the network's work): a CTA's 128 consecutive voxels are R = 128 / w
 // x-rows (y0 .. y0+R-1) of one plane z.  For each chunk of kc input channels
-// the CTA stages once, with cp.async, the 3 (R + 2) x-rows the 27 taps reach:
-// rows y0-1 .. y0+R (circular in y) of the planes z-1, z, z+1 (zeros outside
-// the box), as halo[row][x][kc] bf16.  A step then takes the three taps
+// the CTA stages once, with cp.async, the 3 (R + 2) x-rows the 27 taps reach
+// -- rows y0-1 .. y0+R (circular in y) of the planes z-1, z, z+1 (zeros
+// outside the box), as halo[row][x][kc] bf16 -- together with the chunk's
+// weights of all 27 taps (K-major).  A step then takes the three taps
 // (dx = -1, 0, 1) of one (dz, dy): each thread copies its voxel's shifted row
 // (circular in x) from the halo into the K-major A layout of the step's stage
-// (one copy per tap from shared memory instead of a gather from L2), the
-// stage's weights come with cp.async, and thread 0 issues the MMAs after a
-// CTA barrier, committing them to the stage's mbarrier.  Epilogue as in
-// k_conv3_tc.
+// (one copy per tap from shared memory instead of a gather from L2), and
+// thread 0 issues the MMAs after a CTA barrier, committing them to the
+// stage's mbarrier; the next step's copies overlap those MMAs.  Epilogue as
+// in k_conv3_tc.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncols, int *status)
 {
@@ -497,10 +498,10 @@ __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncol
     const int32_t gp = m0 / plane;
     const int z = gp % g.d, y0 = (m0 - gp * plane) / w;
     const uint32_t a_bytes = (uint32_t)kTcM * kc * 2, b_bytes = (uint32_t)n * kc * 2;
-    const uint32_t stage_bytes = 3u * (a_bytes + b_bytes), sbo = (uint32_t)(kc / 8) * 128u;
-    const uint32_t halo_bytes = 3u * (uint32_t)hrows * (uint32_t)w * (uint32_t)kc * 2u;
-    const uint32_t base = tc::smem_u32(smem), halo = base + 2u * stage_bytes;
-    const unsigned char *halo_p = smem + 2u * stage_bytes;
+    const uint32_t stage_bytes = 3u * a_bytes, sbo = (uint32_t)(kc / 8) * 128u;
+    // shared memory: [2 A stages][27 taps of weights][halo]
+    const uint32_t base = tc::smem_u32(smem), wts = base + 2u * stage_bytes, halo = wts + (uint32_t)kTaps * b_bytes;
+    const unsigned char *halo_p = smem + 2u * stage_bytes + (size_t)kTaps * b_bytes;
     tc::setup(&tmem_slot, full, empty, 2, ncols);
     const uint32_t tmem = tmem_slot;
     const uint32_t id = tc::idesc(kTcM, n, false);
@@ -509,8 +510,9 @@ __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncol
     const int chunks = ci / kc, iters = chunks * 9;
     const int pieces = kc / 8;   // 16-byte pieces of a row of kc channels
 
-    // stage the halo of channel chunk c0 (all threads; cp.async, committed)
-    auto load_halo = [&](int c0) {
+    // stage the halo and the 27 taps' weights of channel chunk c0 (all
+    // threads; cp.async, committed)
+    auto load_chunk = [&](int c0) {
         const int total = 3 * hrows * w * pieces;
         for (int e = tid; e < total; e += 128) {
             const int j = e % pieces, vox = e / pieces;
@@ -525,16 +527,29 @@ __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncol
             const bf16 *src = c < a.ci0 ? a.in0 + (int64_t)v * a.ci0 + c : a.in1 + (int64_t)v * a.ci1 + (c - a.ci0);
             tc::cp16(halo + (uint32_t)e * 16u, valid ? (const void *)src : (const void *)a.in0, valid);
         }
+        for (int e = tid; e < kTaps * n * pieces; e += 128) {
+            const int j = e % pieces, r = (e / pieces) % n, t = e / (pieces * n);
+            const bf16 *src = a.w + ((int64_t)t * n + r) * ci + c0 + 8 * j;
+            tc::cp16(wts + (uint32_t)t * b_bytes + (uint32_t)(r >> 3) * sbo + (uint32_t)j * 128u + (uint32_t)(r & 7) * 16u,
+                     src, true);
+        }
         tc::commit_group();
     };
     bool ok = true;
     for (int it = 0; it < iters && ok; ++it) {
         const int s = it & 1, chunk = it / 9, q = it % 9;
-        const int dz = q / 3 - 1, dy = q % 3 - 1, c0 = chunk * kc;
+        const int dz = q / 3 - 1, dy = q % 3 - 1;
         if (q == 0) {
-            // every thread is past its copies out of the previous chunk's halo
-            // (the barrier of the previous step); restage it
-            load_halo(c0);
+            // the weights of the previous chunk are read by its MMAs: wait for
+            // the last commit (it tracks every earlier MMA) before restaging;
+            // the barrier also covers every thread's copies out of the halo
+            if (it > 0) {
+                int wv = 1;
+                if (tid == 0) wv = tc::wait(&empty[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1), status) ? 1 : 0;
+                ok = __syncthreads_and(wv) != 0;
+                if (!ok) break;
+            }
+            load_chunk(chunk * kc);
             tc::wait_groups(0);
             __syncthreads();
         }
@@ -545,17 +560,6 @@ __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncol
             if (!ok) break;
         }
         const uint32_t st0 = base + (uint32_t)s * stage_bytes;
-        // weights of the three taps for this chunk (K-major, rows of kc)
-        for (int qq = 0; qq < 3; ++qq) {
-            const int t = (dz + 1) * 9 + (dy + 1) * 3 + qq;
-            const uint32_t sb = st0 + 3u * a_bytes + (uint32_t)qq * b_bytes;
-            for (int e = tid; e < n * pieces; e += 128) {
-                const int r = e / pieces, j = e % pieces;
-                const bf16 *src = a.w + ((int64_t)t * n + r) * ci + c0 + 8 * j;
-                tc::cp16(sb + (uint32_t)(r >> 3) * sbo + (uint32_t)j * 128u + (uint32_t)(r & 7) * 16u, src, true);
-            }
-        }
-        tc::commit_group();
         // the three shifted rows of this thread's voxel, from the halo
         if (m0 + tid < V) {
             const int hr = (dz + 1) * hrows + lr + 1 + dy;
@@ -566,13 +570,13 @@ __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncol
                 for (int j = 0; j < pieces; ++j) *reinterpret_cast<uint4 *>(dst + (size_t)j * 128u) = src[j];
             }
         }
-        tc::wait_groups(0);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             for (int qq = 0; qq < 3; ++qq) {
-                const uint32_t sa = st0 + (uint32_t)qq * a_bytes, sb = st0 + 3u * a_bytes + (uint32_t)qq * b_bytes;
+                const int t = (dz + 1) * 9 + (dy + 1) * 3 + qq;
+                const uint32_t sa = st0 + (uint32_t)qq * a_bytes, sb = wts + (uint32_t)t * b_bytes;
                 for (int j = 0; j < kc / 16; ++j)
                     tc::mma(tmem, tc::desc(sa + (uint32_t)j * 256u, 128u, sbo), tc::desc(sb + (uint32_t)j * 256u, 128u, sbo),
                             id, it > 0 || qq > 0 || j > 0);
@@ -614,7 +618,6 @@ __global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncol
             }
         }
     }
-    (void)halo_bytes;
     (void)full;
     tc::teardown(tmem, ncols);
 }
@@ -1107,7 +1110,9 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
     // taps plus the halo of 3 (R + 2) rows
     if ((a.g.w == 32 || a.g.w == 64) && ((int64_t)a.g.h * a.g.w) % kTcM == 0 && a.g.h >= 2) {
         const int R = kTcM / a.g.w;
-        const size_t smem = 2 * 3 * per_tap + (size_t)3 * (R + 2) * a.g.w * kc * 2;
+        // two A stages of three taps, the weights of all 27 taps, the halo
+        const size_t smem = (size_t)2 * 3 * kTcM * kc * 2 + (size_t)kTaps * co * kc * 2 +
+                            (size_t)3 * (R + 2) * a.g.w * kc * 2;
         if (smem <= (size_t)kHaloMaxSmem) {
             static bool hattr = false;
             if (!hattr) {
