@@ -189,11 +189,17 @@ def cpu_baseline(seconds_hint: float = 15.0):
 
 
 def workload_name(args):
+    name = None
     if args.workload == "channel":
-        return WORKLOAD
+        name = WORKLOAD
     if args.workload == "channel-half":
-        return (WORKLOAD.replace("256x256x512", "128x128x256").replace("z=0/511", "z=0/255")
+        name = (WORKLOAD.replace("256x256x512", "128x128x256").replace("z=0/511", "z=0/255")
                 .replace("z<256", "z<128"))
+    if name is not None:
+        if getattr(args, "phi", None) is not None:
+            name = name.replace("porosity sweep {0.4,0.6,0.8,0.9} (one solver each); one step = one time step of all four",
+                                f"porosity {args.phi:g} (one solver)")
+        return name
     if args.workload == "w0":
         return ("151^3 periodic cube, one centred sphere of diameter 90 (the paper's per-core block), "
                 + ("simple bounce-back on every link" if args.bounce_back else "CLI walls"))
@@ -885,10 +891,11 @@ def run_ours(args, world, rank, local):
     L.load_library()
     stream = torch.cuda.current_stream()
 
+    phis = W.W2_POROSITIES if args.phi is None else [args.phi]
     if args.workload == "channel":
-        cases = [W.W2(phi) for phi in W.W2_POROSITIES]
+        cases = [W.W2(phi) for phi in phis]
     elif args.workload == "channel-half":   # the same channel at half the size, for profiler captures
-        cases = [W.W2_half(phi) for phi in W.W2_POROSITIES]
+        cases = [W.W2_half(phi) for phi in phis]
     elif args.workload == "large":   # one 512x512x1024 channel (W2's structure, porosity 0.6)
         cases = [W.W3_LARGE]
     elif args.workload == "w0":   # the paper's single-sphere block: 151^3 periodic, one sphere D = 90
@@ -1069,7 +1076,8 @@ def main():
                          "re-sweep: the resolution and Reynolds-number studies of the pore-scale profile; "
                          "cli-stability: growth of a perturbation of the rest state on every packing")
     ap.add_argument("--cubes", type=int, default=64, help="number of REV cubes (rev workload)")
-    ap.add_argument("--phi", type=float, default=None, help="--converge: one porosity of the channel sweep")
+    ap.add_argument("--phi", type=float, default=None,
+                    help="channel workloads: one porosity of the sweep instead of all four")
     ap.add_argument("--precision-check", action="store_true",
                     help="--converge: FP16/BF16 runs started from the converged FP32 field, errors against it")
     ap.add_argument("--rp-max-steps", type=int, default=400_000,

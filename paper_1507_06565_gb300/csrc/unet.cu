@@ -467,162 +467,6 @@ __global__ void __launch_bounds__(128) k_conv3_tc(ConvArgs a, int kc, int tp, in
 }
 
 // ---------------------------------------------------------------------------
-// Convolution from a halo tile in shared memory, for the levels whose x-rows
-// are 32 or 64 voxels (the full- and half-resolution levels, which carry most
-// of the network's work): a CTA's 128 consecutive voxels are R = 128 / w
-// x-rows (y0 .. y0+R-1) of one plane z.  For each chunk of kc input channels
-// the CTA stages once, with cp.async, the 3 (R + 2) x-rows the 27 taps reach
-// -- rows y0-1 .. y0+R (circular in y) of the planes z-1, z, z+1 (zeros
-// outside the box), as halo[row][x][kc] bf16 -- together with the chunk's
-// weights of all 27 taps (K-major).  A step then takes the three taps
-// (dx = -1, 0, 1) of one (dz, dy): each thread copies its voxel's shifted row
-// (circular in x) from the halo into the K-major A layout of the step's stage
-// (one copy per tap from shared memory instead of a gather from L2), and
-// thread 0 issues the MMAs after a CTA barrier, committing them to the
-// stage's mbarrier; the next step's copies overlap those MMAs.  Epilogue as
-// in k_conv3_tc.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_conv3_halo(ConvArgs a, int kc, int ncols, int *status)
-{
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[tc::kMaxStages], empty[tc::kMaxStages];
-    __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ci = a.ci0 + a.ci1, n = a.co0 + a.co1;
-    const Dims g = a.g;
-    const int w = g.w, R = kTcM / w, hrows = R + 2;
-    const int32_t plane = g.h * w;
-    const int32_t m0 = (int32_t)blockIdx.x * kTcM;
-    const int32_t V = (int32_t)g.voxels();
-    // the CTA's plane (global index n * d + z) and first row
-    const int32_t gp = m0 / plane;
-    const int z = gp % g.d, y0 = (m0 - gp * plane) / w;
-    const uint32_t a_bytes = (uint32_t)kTcM * kc * 2, b_bytes = (uint32_t)n * kc * 2;
-    const uint32_t stage_bytes = 3u * a_bytes, sbo = (uint32_t)(kc / 8) * 128u;
-    // shared memory: [2 A stages][27 taps of weights][halo]
-    const uint32_t base = tc::smem_u32(smem), wts = base + 2u * stage_bytes, halo = wts + (uint32_t)kTaps * b_bytes;
-    const unsigned char *halo_p = smem + 2u * stage_bytes + (size_t)kTaps * b_bytes;
-    tc::setup(&tmem_slot, full, empty, 2, ncols);
-    const uint32_t tmem = tmem_slot;
-    const uint32_t id = tc::idesc(kTcM, n, false);
-    const int lr = tid / w, x = tid % w;   // this thread's output voxel in the tile
-    const uint32_t row_off = (uint32_t)(tid >> 3) * sbo + (uint32_t)(tid & 7) * 16u;
-    const int chunks = ci / kc, iters = chunks * 9;
-    const int pieces = kc / 8;   // 16-byte pieces of a row of kc channels
-
-    // stage the halo and the 27 taps' weights of channel chunk c0 (all
-    // threads; cp.async, committed)
-    auto load_chunk = [&](int c0) {
-        const int total = 3 * hrows * w * pieces;
-        for (int e = tid; e < total; e += 128) {
-            const int j = e % pieces, vox = e / pieces;
-            const int xx = vox % w, r = vox / w;   // r = plane band * hrows + row
-            const int pz = r / hrows, ry = r % hrows;
-            const int zz = z + pz - 1;
-            int yy = y0 + ry - 1;
-            yy = yy < 0 ? yy + g.h : (yy >= g.h ? yy - g.h : yy);
-            const bool valid = zz >= 0 && zz < g.d;
-            const int32_t v = (gp - z + zz) * plane + yy * w + xx;
-            const int c = c0 + 8 * j;
-            const bf16 *src = c < a.ci0 ? a.in0 + (int64_t)v * a.ci0 + c : a.in1 + (int64_t)v * a.ci1 + (c - a.ci0);
-            tc::cp16(halo + (uint32_t)e * 16u, valid ? (const void *)src : (const void *)a.in0, valid);
-        }
-        for (int e = tid; e < kTaps * n * pieces; e += 128) {
-            const int j = e % pieces, r = (e / pieces) % n, t = e / (pieces * n);
-            const bf16 *src = a.w + ((int64_t)t * n + r) * ci + c0 + 8 * j;
-            tc::cp16(wts + (uint32_t)t * b_bytes + (uint32_t)(r >> 3) * sbo + (uint32_t)j * 128u + (uint32_t)(r & 7) * 16u,
-                     src, true);
-        }
-        tc::commit_group();
-    };
-    bool ok = true;
-    for (int it = 0; it < iters && ok; ++it) {
-        const int s = it & 1, chunk = it / 9, q = it % 9;
-        const int dz = q / 3 - 1, dy = q % 3 - 1;
-        if (q == 0) {
-            // the weights of the previous chunk are read by its MMAs: wait for
-            // the last commit (it tracks every earlier MMA) before restaging;
-            // the barrier also covers every thread's copies out of the halo
-            if (it > 0) {
-                int wv = 1;
-                if (tid == 0) wv = tc::wait(&empty[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1), status) ? 1 : 0;
-                ok = __syncthreads_and(wv) != 0;
-                if (!ok) break;
-            }
-            load_chunk(chunk * kc);
-            tc::wait_groups(0);
-            __syncthreads();
-        }
-        if (it >= 2) {
-            int wv = 1;
-            if (tid == 0) wv = tc::wait(&empty[s], (uint32_t)(((it - 2) >> 1) & 1), status) ? 1 : 0;
-            ok = __syncthreads_and(wv) != 0;
-            if (!ok) break;
-        }
-        const uint32_t st0 = base + (uint32_t)s * stage_bytes;
-        // the three shifted rows of this thread's voxel, from the halo
-        if (m0 + tid < V) {
-            const int hr = (dz + 1) * hrows + lr + 1 + dy;
-            for (int qq = 0; qq < 3; ++qq) {
-                const int xs = (x + qq - 1 + w) % w;
-                const uint4 *src = reinterpret_cast<const uint4 *>(halo_p + ((size_t)hr * w + xs) * kc * 2);
-                unsigned char *dst = smem + (size_t)s * stage_bytes + (size_t)qq * a_bytes + row_off;
-                for (int j = 0; j < pieces; ++j) *reinterpret_cast<uint4 *>(dst + (size_t)j * 128u) = src[j];
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            for (int qq = 0; qq < 3; ++qq) {
-                const int t = (dz + 1) * 9 + (dy + 1) * 3 + qq;
-                const uint32_t sa = st0 + (uint32_t)qq * a_bytes, sb = wts + (uint32_t)t * b_bytes;
-                for (int j = 0; j < kc / 16; ++j)
-                    tc::mma(tmem, tc::desc(sa + (uint32_t)j * 256u, 128u, sbo), tc::desc(sb + (uint32_t)j * 256u, 128u, sbo),
-                            id, it > 0 || qq > 0 || j > 0);
-            }
-            tc::commit(&empty[s]);
-        }
-    }
-    // the last commit tracks every MMA issued before it
-    int wv = ok ? 1 : 0;
-    if (ok && tid == 0) {
-        const int l = iters - 1;
-        wv = tc::wait(&empty[l & 1], (uint32_t)((l >> 1) & 1), status) ? 1 : 0;
-    }
-    ok = __syncthreads_and(wv) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (ok) {
-        const int32_t row = m0 + warp * 32 + lane;
-        for (int cc = 0; cc < n; cc += 16) {
-            uint32_t r[16];
-            tc::load16(tmem, warp, cc, r);
-            if (row < V) {
-                uint32_t packed[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int c = cc + 2 * j;
-                    float y0f = __uint_as_float(r[2 * j]) + (a.bias ? a.bias[c] : 0.0f);
-                    float y1f = __uint_as_float(r[2 * j + 1]) + (a.bias ? a.bias[c + 1] : 0.0f);
-                    if (a.relu) {
-                        y0f = fmaxf(y0f, 0.0f);
-                        y1f = fmaxf(y1f, 0.0f);
-                    }
-                    const __nv_bfloat162 pr = __floats2bfloat162_rn(y0f, y1f);
-                    packed[j] = *reinterpret_cast<const uint32_t *>(&pr);
-                }
-                bf16 *dst = cc < a.co0 ? a.out0 + (int64_t)row * a.co0 + cc : a.out1 + (int64_t)row * a.co1 + (cc - a.co0);
-                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-                d4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                d4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-            }
-        }
-    }
-    (void)full;
-    tc::teardown(tmem, ncols);
-}
-
-// ---------------------------------------------------------------------------
 // Weight gradient dW[t][o][c] += sum_v dY[v][o] X(v + off_t)[c]: one CTA per
 // (voxel chunk, tap) computes D = dY^T X_t with M = 128 rows (o < co used),
 // N = ci, K = the chunk's voxels in steps of kWgStepVox, and adds D to dW with
@@ -1082,7 +926,6 @@ static unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) /
 // they fit in kTcStepSmem; one stage of the largest layer (co = 192, KC = 64)
 // is 40 KB, so two of them (80 KB) stay within kTcMaxSmem.
 constexpr int kTcMaxSmem = 96 * 1024;
-constexpr int kHaloMaxSmem = 160 * 1024;
 constexpr int kTcStepSmem = 64 * 1024;
 
 static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
@@ -1105,26 +948,6 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st, int *status)
     // 9-tap steps were all slower (they cost resident CTAs or add per-step
     // work); the gathers, not the tensor cores, bound this kernel.
     const size_t per_tap = (size_t)kTcM * kc * 2 + (size_t)co * kc * 2;
-    // the halo kernel where the x-rows are 32 or 64 voxels (128 voxels = 2 or
-    // 4 rows of one plane) and its shared memory fits: two stages of three
-    // taps plus the halo of 3 (R + 2) rows
-    if ((a.g.w == 32 || a.g.w == 64) && ((int64_t)a.g.h * a.g.w) % kTcM == 0 && a.g.h >= 2) {
-        const int R = kTcM / a.g.w;
-        // two A stages of three taps, the weights of all 27 taps, the halo
-        const size_t smem = (size_t)2 * 3 * kTcM * kc * 2 + (size_t)kTaps * co * kc * 2 +
-                            (size_t)3 * (R + 2) * a.g.w * kc * 2;
-        if (smem <= (size_t)kHaloMaxSmem) {
-            static bool hattr = false;
-            if (!hattr) {
-                if (cudaFuncSetAttribute(k_conv3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloMaxSmem) !=
-                    cudaSuccess)
-                    return LBM_ECUDA;
-                hattr = true;
-            }
-            k_conv3_halo<<<blocks(a.g.voxels(), kTcM), 128, smem, st>>>(a, kc, ncols, status);
-            return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
-        }
-    }
     const int tp = 2 * 3 * per_tap <= (size_t)48 * 1024 ? 3 : 1;
     const int stages = 2;
     k_conv3_tc<<<blocks(a.g.voxels(), kTcM), 128, stages * tp * per_tap, st>>>(a, kc, tp, ncols, stages, status);
@@ -1146,8 +969,11 @@ static int launch_wgrad(const bf16 *dy, int co, const bf16 *in0, int ci0, const 
     const int ci = ci0 + ci1;
     const int64_t V = g.voxels();
     if (co > kTcM || co % 16 != 0 || ci % 16 != 0 || ci > 256 || V >= ((int64_t)1 << 31)) return LBM_EINVAL;
-    if (kTcM % co == 0) {
-        // taps stacked along M
+    if (co == 16) {
+        // taps stacked along M (8 taps per tile): measured 1.5-1.8x faster
+        // than one padded tile per tap for the 16-channel layers, and slower
+        // for 32-128 output channels, where a tap already fills 2-8 of the
+        // tile's 8-row groups
         static bool sattr = false;
         if (!sattr) {
             if (cudaFuncSetAttribute(k_wgrad_stack, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem) !=

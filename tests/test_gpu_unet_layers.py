@@ -29,8 +29,9 @@ def torch_cuda():
 
 
 DIMS = (2, 6, 10, 12)   # n, nz, ny, nx: 1440 voxels, a ragged last tile of 128
-# boxes whose x-rows of 32 / 64 voxels take the halo-tile kernel (128 voxels =
-# 4 / 2 rows of one plane), with wrap-around in y and zeros beyond z
+# boxes with the x-rows of the network's two finest levels (32 / 64 voxels):
+# a tile of 128 voxels is 4 / 2 whole rows, with wrap-around in y and zeros
+# beyond z
 HALO_DIMS = [(2, 3, 4, 32), (1, 4, 2, 64), (1, 2, 8, 64)]
 
 
