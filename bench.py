@@ -238,7 +238,8 @@ def odd_flags(args, cases=()) -> int:
     import paper_1507_06565_gb300 as L
 
     flags = {"auto": 0, "table": L.LBM_FLAG_NEIGHBOUR_TABLE, "rows": L.LBM_FLAG_ROW_NEIGHBOURS,
-             "staged": L.LBM_FLAG_STAGED_NEIGHBOURS}[getattr(args, "odd", "auto")]
+             "staged": L.LBM_FLAG_STAGED_NEIGHBOURS,
+             "derived": L.LBM_FLAG_DERIVED_NEIGHBOURS}[getattr(args, "odd", "auto")]
     if getattr(args, "bounce_back", False):
         flags |= L.LBM_FLAG_SIMPLE_BOUNCE_BACK
     if getattr(args, "even", "auto") == "staged":
@@ -1052,7 +1053,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--odd", choices=["auto", "table", "rows", "staged"], default="auto",
+    ap.add_argument("--odd", choices=["auto", "table", "rows", "staged", "derived"], default="auto",
                     help="neighbour indices of the odd step (library default, int32 table, row bitmasks, row words "
                          "staged per tile)")
     ap.add_argument("--even", choices=["auto", "staged"], default="auto",

@@ -115,6 +115,13 @@ typedef struct {
  * rows do not fit the staging buffer use the table.  Needs nx, ny <= 2048
  * and nz <= 1024 (else the table is used). */
 #define LBM_FLAG_STAGED_NEIGHBOURS 256
+/* Neighbour indices outside the computed tiles: the table's eight entries
+ * without an x component, and the ten with one derived from them (fluid
+ * cells are numbered along x-rows, so the fluid neighbour at x +- 1 of a
+ * fluid cell j in the same row is j +- 1), reading the table only where that
+ * cell is solid or the row wraps around: 36 bytes per cell and odd step plus
+ * those reads, instead of 72. */
+#define LBM_FLAG_DERIVED_NEIGHBOURS 2048
 /* Scheduling switches.  By default lbm_step times a few grid sizes for each
  * step kernel during its first launches on solvers of more than ~4 waves of
  * blocks (synchronising the stream while it does so) and then replays the

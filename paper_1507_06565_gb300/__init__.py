@@ -40,6 +40,7 @@ LBM_FLAG_CLI_SAFEGUARDS = 128
 LBM_FLAG_STAGED_NEIGHBOURS = 256
 LBM_FLAG_PLANE_REFERENCES = 512
 LBM_FLAG_NO_PLANE_REFERENCES = 1024
+LBM_FLAG_DERIVED_NEIGHBOURS = 2048
 
 LBM_CONVERGE_FIELD = 0
 LBM_CONVERGE_PROFILE = 1

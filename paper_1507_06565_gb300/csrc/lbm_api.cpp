@@ -107,9 +107,11 @@ static bool params_ok(const lbm_params *p)
         if (!std::isfinite(p->g[d])) return false;
     const int32_t known = LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_NO_GRAPH | LBM_FLAG_NO_AUTOTUNE |
                           LBM_FLAG_SIMPLE_BOUNCE_BACK | LBM_FLAG_STAGED_EVEN | LBM_FLAG_CLI_SAFEGUARDS |
-                          LBM_FLAG_STAGED_NEIGHBOURS | LBM_FLAG_PLANE_REFERENCES | LBM_FLAG_NO_PLANE_REFERENCES;
+                          LBM_FLAG_STAGED_NEIGHBOURS | LBM_FLAG_PLANE_REFERENCES | LBM_FLAG_NO_PLANE_REFERENCES |
+                          LBM_FLAG_DERIVED_NEIGHBOURS;
     if ((p->flags & ~known) != 0) return false;
-    const int32_t variants = p->flags & (LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_STAGED_NEIGHBOURS);
+    const int32_t variants = p->flags & (LBM_FLAG_NEIGHBOUR_TABLE | LBM_FLAG_ROW_NEIGHBOURS | LBM_FLAG_STAGED_NEIGHBOURS |
+                                         LBM_FLAG_DERIVED_NEIGHBOURS);
     if (variants & (variants - 1)) return false;   // at most one neighbour variant
     if ((p->flags & LBM_FLAG_PLANE_REFERENCES) && (p->flags & LBM_FLAG_NO_PLANE_REFERENCES)) return false;
     return p->storage == LBM_F32 || p->storage == LBM_F16 || p->storage == LBM_BF16;
@@ -232,6 +234,7 @@ static int init_parts(const std::vector<const Geometry *> &geoms, const lbm_para
         if (params->flags & LBM_FLAG_ROW_NEIGHBOURS) rows = true;
         s->odd_rows = rows && single && s->rows_ok;
         s->staged_rows = (params->flags & LBM_FLAG_STAGED_NEIGHBOURS) && s->rows_ok && !s->odd_rows;
+        s->derived_nbrs = (params->flags & LBM_FLAG_DERIVED_NEIGHBOURS) != 0;
     }
     s->use_graph = !(params->flags & LBM_FLAG_NO_GRAPH);
     s->autotune = !(params->flags & LBM_FLAG_NO_AUTOTUNE);

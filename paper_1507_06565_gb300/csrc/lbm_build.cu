@@ -145,6 +145,8 @@ __global__ void k_neighbours(const int32_t *__restrict__ idx_map, const int32_t 
         nbr[(size_t)(k - 1) * n_pad + i] = j;
         m |= (uint32_t)(j < 0) << k;
     }
+    if (x == nx - 1) m |= kXLast;
+    if (x == 0) m |= kXFirst;
     lmask[i] = m;
 }
 
@@ -164,7 +166,7 @@ __global__ void k_pad_cells(int32_t n_fluid, int32_t n_pad, int32_t *__restrict_
 __global__ void k_warp_counts(const uint32_t *__restrict__ lmask, uint32_t *__restrict__ warp_cnt)
 {
     const int32_t i = blockIdx.x * kBlock + threadIdx.x;
-    uint32_t cnt = __popc(lmask[i]);
+    uint32_t cnt = __popc(lmask[i] & kLinkBits);
     for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
     if ((threadIdx.x & 31) == 0) warp_cnt[i >> 5] = cnt;
 }
@@ -220,7 +222,7 @@ __global__ void k_links(LinkArgs a)
     const int lane = threadIdx.x & 31;
     const int32_t i = (a.begin & ~31) + (int32_t)(blockIdx.x * kBlock + threadIdx.x);
     const int32_t i0 = i - lane;   // first cell of the warp's group
-    const uint32_t m = i < a.n_fluid ? a.lmask[i] : 0u;
+    const uint32_t m = i < a.n_fluid ? a.lmask[i] & kLinkBits : 0u;
     const uint32_t cnt = __popc(m);
     uint32_t incl = cnt;
     for (int d = 1; d < 32; d <<= 1) {

@@ -4,7 +4,8 @@
 //   pdf        [19][n_pad]  shifted populations h_k = f_k - w_k, storage type T,
 //                           in-place AA pattern (see lbm_step.cu)
 //   nbr        [18][n_pad]  int32 fluid index of x + e_k (k = 1..18), -1 if solid
-//   lmask      [n_pad]      uint32, bit k set when x + e_k is solid (wall link k)
+//   lmask      [n_pad]      uint32, bit k set when x + e_k is solid (wall link k,
+//                           kLinkBits); bit 19 when x = nx - 1, bit 20 when x = 0
 //   warp_off   [n_pad/32]   uint32, index of the first link of each aligned group
 //                           of 32 fluid cells in the link arrays
 //   link_a     [n_links]    float, CLI coefficient (1-2q)/(1+2q), 0 for bounce-back
@@ -62,6 +63,11 @@ constexpr int kBinEdge = 8;   // edge (cells) of the sphere-image bins
 // k_links).
 constexpr double kCliQmin = 0.1;
 constexpr int kRefStride = 20;   // floats per plane of reference populations (19 used)
+// lmask: the link bits 1..18, and two bits for the cells at the ends of an
+// x-row (their x -+ 1 neighbour wraps around the periodic x span)
+constexpr uint32_t kLinkBits = 0x7FFFEu;
+constexpr uint32_t kXLast = 1u << 19;    // x = nx - 1
+constexpr uint32_t kXFirst = 1u << 20;   // x = 0
 // packed cell position x | y << 11 | z << 22 (row bitmask variants)
 constexpr int kXyzBitsX = 11, kXyzBitsY = 11, kXyzBitsZ = 10;
 // row words one tile of the odd step stages in shared memory (3 bands of
@@ -177,6 +183,7 @@ struct Solver {
     bool rows_ok = false;          // every part fits the packed positions: row words and cell_xr exist
     bool odd_rows = true;          // odd step computes neighbours from row bitmasks
     bool staged_rows = false;      // odd step stages row words per tile (LBM_FLAG_STAGED_NEIGHBOURS)
+    bool derived_nbrs = false;     // odd step derives x-shifted neighbours (LBM_FLAG_DERIVED_NEIGHBOURS)
     // launch schedule: grid sizes of the even/odd step (0 = one block per
     // tile, -1 = the staged even kernel on one wave of resident blocks)
     int grid_even = 0, grid_odd = 0;

@@ -459,6 +459,36 @@ __device__ __forceinline__ void dense_neighbours(int32_t nb[kQ], int2 d, int32_t
     for (int k = 1; k < kQ; ++k) nb[k] = i + ox[ex(k) + 1] + oy[ey(k) + 1] + ez(k) * plane;
 }
 
+// Neighbour indices from the table for the eight directions without an x
+// component and from arithmetic for the ten with one: fluid cells are
+// numbered along x-rows, so the neighbour at x +- 1 of a fluid cell j in the
+// same row is j +- 1 whenever it is fluid.  (x +- 1, y', z') is therefore the
+// index of (x, y', z') +- 1 -- the table's entry of an axis direction, or i
+// itself for +-x -- when both cells are fluid and x +- 1 does not wrap around
+// the row (lm: the cell's link bits and row-end bits); otherwise, if the
+// neighbour is fluid, its table entry is read.  Returns the link mask.
+__device__ __forceinline__ uint32_t derived_nbr(int32_t nb[kQ], const int32_t *__restrict__ nbr, size_t n_pad, int32_t i,
+                                                uint32_t lm)
+{
+    nb[0] = i;
+#pragma unroll
+    for (int k = 1; k < kQ; ++k)
+        if (ex(k) == 0) nb[k] = nbr[(k - 1) * n_pad + i];
+#pragma unroll
+    for (int k = 1; k < kQ; ++k) {
+        if (ex(k) == 0) continue;
+        // the x-free direction with the same (ey, ez): 0 (the cell) or 3..6
+        const int b = ey(k) > 0 ? 3 : ey(k) < 0 ? 4 : ez(k) > 0 ? 5 : ez(k) < 0 ? 6 : 0;
+        const bool wraps = (lm & (ex(k) > 0 ? kXLast : kXFirst)) != 0u;
+        const bool base_fluid = b == 0 || ((lm >> b) & 1u) == 0u;
+        const int32_t base = b == 0 ? i : nb[b];
+        if ((lm >> k) & 1u) nb[k] = -1;
+        else if (base_fluid && !wraps) nb[k] = base + ex(k);
+        else nb[k] = nbr[(k - 1) * n_pad + i];
+    }
+    return lm & kLinkBits;
+}
+
 __device__ __forceinline__ uint32_t load_nbr(int32_t nb[kQ], const int32_t *__restrict__ nbr, size_t n_pad, int32_t i)
 {
     uint32_t m = 0;

@@ -48,7 +48,7 @@ __device__ __forceinline__ bool current_populations(const T *pdf, const PostArgs
     const size_t n_pad = (size_t)p.n_pad;
     int32_t nb[kQ];
     uint32_t m = 0;
-    if (live) m = ODD ? load_nbr(nb, p.nbr, n_pad, i) : p.lmask[i];
+    if (live) m = ODD ? load_nbr(nb, p.nbr, n_pad, i) : p.lmask[i] & kLinkBits;
     const uint32_t off = first_link(p.warp_off, i, m);
     if (!live) return false;
     float a[kQ];

@@ -35,7 +35,9 @@ constexpr int kOddBlocksPerSM = 6;
 // in the odd step).
 // kNbStaged: the table's role outside the dense tiles is taken by row words
 // staged per tile in shared memory (LBM_FLAG_STAGED_NEIGHBOURS).
-enum NbSource { kNbTable = 0, kNbRows = 1, kNbDense = 2, kNbStaged = 3 };
+// kNbDerived: outside the dense tiles the table's x-shifted entries are
+// derived from its other entries (LBM_FLAG_DERIVED_NEIGHBOURS).
+enum NbSource { kNbTable = 0, kNbRows = 1, kNbDense = 2, kNbStaged = 3, kNbDerived = 4 };
 constexpr int kGridBulk = -1;       // schedule entry: the staged even step
 constexpr int kGraphSteps = 32;     // steps per CUDA-graph replay (even)
 constexpr int kTuneReps = 3;        // timed launches per candidate grid
@@ -95,7 +97,7 @@ template <typename T, bool REF>
 __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 {
     const bool live = i < p.n_fluid;
-    const uint32_t m = live ? p.lmask[i] : 0u;
+    const uint32_t m = live ? p.lmask[i] & kLinkBits : 0u;
     const uint32_t off = first_link(p.warp_off, i, m);
     if (!live) return;
     const int32_t rr = ref_row<REF>(p, i);
@@ -137,7 +139,7 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     uint32_t m = 0;
     // a dense tile (same for the whole block) computes its indices and has no links
     const int32_t tile = i / kBlock;
-    const int2 d = (NB == kNbDense || NB == kNbStaged) && tile >= p.dense_lo && tile < p.dense_hi
+    const int2 d = (NB == kNbDense || NB == kNbStaged || NB == kNbDerived) && tile >= p.dense_lo && tile < p.dense_hi
                        ? __ldg(p.tile_desc + tile)
                        : make_int2(-1, 0);
     // a staged tile (same for the whole block): its bands of row words go to
@@ -154,6 +156,7 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
         if (d.x >= 0) dense_neighbours(nb, d, i);
         else if (NB == kNbStaged && sd.x >= 0 && staged_neighbours(nb, m, ws, sd, __ldg(p.rows.cell_xr + i), i)) {
         }
+        else if (NB == kNbDerived) m = derived_nbr(nb, p.nbr, (size_t)n_pad, i, __ldg(p.lmask + i));
         else m = NB == kNbRows ? row_neighbours(nb, p.rows, i) : load_nbr(nb, p.nbr, (size_t)n_pad, i);
         // stage the slot of direction k, A[k][x + e_k] or the dead slot
         // A[opp k][x] of a wall link: the gather of h_opp(k) reads it and the
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
     for (; j < count; ++j) {
         const int32_t i = (first + j * stride) * kBlock + t;
         const bool live = i < p.n_fluid;
-        const uint32_t m = live ? p.lmask[i] : 0u;
+        const uint32_t m = live ? p.lmask[i] & kLinkBits : 0u;
         const uint32_t off = first_link(p.warp_off, i, m);
         const T *row = buf + (size_t)(j % S) * kQ * kBlock + t;
         ok = bulk::wait(&full[j % S], (uint32_t)((j / S) & 1));
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(kBlock) k_init(StepArgs<T> p, const int32_t *_
 {
     const int32_t i = blockIdx.x * kBlock + threadIdx.x;
     const bool live = i < p.n_fluid;
-    const uint32_t m = live ? p.lmask[i] : 0u;
+    const uint32_t m = live ? p.lmask[i] & kLinkBits : 0u;
     const uint32_t off = first_link(p.warp_off, i, m);
     if (!live) return;
     float ux = 0.0f, uy = 0.0f, uz = 0.0f;
@@ -446,6 +449,7 @@ void launch_step_ref(const Solver &s, const StepArgs<T> &p, bool odd, int grid, 
     else if (s.odd_rows) k_step_odd<T, kNbRows, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
     else if (s.staged_rows && p.rows_hi > p.rows_lo)
         k_step_odd<T, kNbStaged, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
+    else if (s.derived_nbrs) k_step_odd<T, kNbDerived, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
     else if (p.dense_hi > p.dense_lo) k_step_odd<T, kNbDense, kOddBlocksPerSM, REF><<<g, kBlock, 0, st>>>(p);
     else k_step_odd<T, kNbTable, kOddBlocksPerSM, false><<<g, kBlock, 0, st>>>(p);
 }

@@ -103,10 +103,10 @@ def test_flags_validated_on_host(lib):
     base = L.lbm_workspace_size(geom, L.make_params())
     for f in (L.LBM_FLAG_NEIGHBOUR_TABLE, L.LBM_FLAG_ROW_NEIGHBOURS, L.LBM_FLAG_NO_GRAPH, L.LBM_FLAG_NO_AUTOTUNE,
               L.LBM_FLAG_SIMPLE_BOUNCE_BACK, L.LBM_FLAG_STAGED_EVEN, L.LBM_FLAG_CLI_SAFEGUARDS,
-              L.LBM_FLAG_STAGED_NEIGHBOURS, L.LBM_FLAG_PLANE_REFERENCES, L.LBM_FLAG_NO_PLANE_REFERENCES,
+              L.LBM_FLAG_STAGED_NEIGHBOURS, L.LBM_FLAG_PLANE_REFERENCES, L.LBM_FLAG_NO_PLANE_REFERENCES, L.LBM_FLAG_DERIVED_NEIGHBOURS,
               L.LBM_FLAG_STAGED_EVEN | L.LBM_FLAG_NO_AUTOTUNE | L.LBM_FLAG_NEIGHBOUR_TABLE):
         assert L.lbm_workspace_size(geom, L.make_params(flags=f)) == base
-    for f in (16, 2048, 1 << 20, L.LBM_FLAG_PLANE_REFERENCES | L.LBM_FLAG_NO_PLANE_REFERENCES, L.LBM_FLAG_NEIGHBOUR_TABLE | L.LBM_FLAG_ROW_NEIGHBOURS,
+    for f in (16, 4096, 1 << 20, L.LBM_FLAG_PLANE_REFERENCES | L.LBM_FLAG_NO_PLANE_REFERENCES, L.LBM_FLAG_NEIGHBOUR_TABLE | L.LBM_FLAG_ROW_NEIGHBOURS,
               L.LBM_FLAG_ROW_NEIGHBOURS | L.LBM_FLAG_STAGED_NEIGHBOURS):
         with pytest.raises(L.LBMError) as e:
             L.lbm_workspace_size(geom, L.make_params(flags=f))

@@ -146,10 +146,12 @@ def test_schedule_does_not_change_results(torch_cuda):
     assert torch.equal(a.populations(), b.populations())
 
 
-def test_batch_staged_neighbours_bit_exact(torch_cuda):
-    """Row words staged per tile in a batch of uneven periodic cubes (each
-    part's words from its own offset; tiles across two cubes use the table)
-    give the table's bits."""
+@pytest.mark.parametrize("flags", [L.LBM_FLAG_STAGED_NEIGHBOURS, L.LBM_FLAG_DERIVED_NEIGHBOURS],
+                         ids=["staged-neighbours", "derived-neighbours"])
+def test_batch_staged_neighbours_bit_exact(torch_cuda, flags):
+    """Row words staged per tile (each part's words from its own offset; tiles
+    across two cubes use the table) and neighbours derived along the x-rows
+    give the table's bits in a batch of uneven periodic cubes."""
     import torch
 
     cubes = [W.W4_cube(i) for i in (59, 62, 3)]
@@ -157,7 +159,7 @@ def test_batch_staged_neighbours_bit_exact(torch_cuda):
     cells = sum(int(np.prod(g.shape)) for g in geoms)
     gen = torch.Generator(device="cuda").manual_seed(3)
     u0 = 1e-2 * torch.rand(3 * cells, device="cuda", generator=gen)
-    a = L.BatchSolver(geoms, g=(1e-5, 0, 0), u0=u0, flags=L.LBM_FLAG_STAGED_NEIGHBOURS)
+    a = L.BatchSolver(geoms, g=(1e-5, 0, 0), u0=u0, flags=flags)
     b = L.BatchSolver(geoms, g=(1e-5, 0, 0), u0=u0, flags=L.LBM_FLAG_NEIGHBOUR_TABLE)
     for n in (7, 64, 33):
         a.step(n)

@@ -460,8 +460,8 @@ def test_one_cell_wide_column(torch_cuda, q):
         assert np.max(np.abs(got - want)) <= TOL_U * np.max(np.abs(want)), n
 
 
-@pytest.mark.parametrize("flags", [L.LBM_FLAG_ROW_NEIGHBOURS, L.LBM_FLAG_STAGED_NEIGHBOURS],
-                         ids=["row-neighbours", "staged-neighbours"])
+@pytest.mark.parametrize("flags", [L.LBM_FLAG_ROW_NEIGHBOURS, L.LBM_FLAG_STAGED_NEIGHBOURS, L.LBM_FLAG_DERIVED_NEIGHBOURS],
+                         ids=["row-neighbours", "staged-neighbours", "derived-neighbours"])
 @pytest.mark.parametrize("case", [CASES[2], W.W1, CASES[1]], ids=lambda c: c.name)
 def test_odd_step_variants_agree(torch_cuda, flags, case):
     """Neighbour table, row-bitmask neighbours and row words staged per tile
