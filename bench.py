@@ -35,13 +35,14 @@ METRIC = "fluid MLUPS (D3Q19 TRT + CLI stream-collide; HBM roofline fraction in 
 WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlapping r=8 spheres, "
             "porosity sweep {0.4,0.6,0.8,0.9} (one solver each); one step = one time step of all four")
 # measured DRAM read + write bytes per fluid cell of one launch (FP32 storage,
-# neighbour table outside the dense tiles): ncu on the default command,
-# full-grid launches of all four solvers (see
-# profiles/step_kernels_channel_256x256x512_dram.txt)
-MEASURED_DRAM_B_PER_FLUP = {"even": 155.1, "odd": 181.3}
-# the same for the 64 batched REV cubes (table-only odd step,
-# profiles/step_kernels_rev_64cubes_dram.txt)
-MEASURED_DRAM_B_PER_FLUP_REV = {"even": 158.5, "odd": 226.8}
+# neighbour table outside the dense tiles): ncu on one full-size solver of the
+# sweep (porosity 0.6, 26.7 M fluid cells), applied per fluid cell to all four
+# (profiles/step_kernels_channel_256x256x512_phi06_dram.txt)
+MEASURED_DRAM_B_PER_FLUP = {"even": 155.5, "odd": 180.3}
+# the same for the batched REV cubes (table-only odd step), taken on the first
+# 8 cubes (11.2 M fluid cells, far above L2) and applied per fluid cell to the
+# 64-cube batch (profiles/step_kernels_rev_8cubes_dram.txt)
+MEASURED_DRAM_B_PER_FLUP_REV = {"even": 153.2, "odd": 222.3}
 # bounded samples of the workload for the CPU oracle: same sphere radius,
 # porosity and channel structure at a reduced box
 SAMPLE = W.Channel("W2-shaped sample 128x128x256 r=8 phi=0.6", 128, 128, 256, 1.0, 128.0, 8.0, 8.0, 0.6, True, 2060)
@@ -742,6 +743,9 @@ def run_surrogate(args):
             "value": warm, "unit": "s", "higher_is_better": False, "cold_s": cold, "speedup": cold / warm,
             "steps_cold": [r["cold"]["steps"] for r in rows], "steps_warm": [r["warm"]["steps"] for r in rows],
             "k_rel_diff_max": max(r["k_rel_diff"] for r in rows),
+            "k_err_warm_max": max(r["k_err_warm"] for r in rows),
+            "k_err_cold_max": max(r["k_err_cold"] for r in rows),
+            "k_reference": "cold run continued, untimed, for 4 decay times of the slowest viscous mode",
             "dtype": "f32 LBM, bf16/fp32 network", "data": "synthetic",
             "config": {"workload": f"{shape[0]}x{shape[1]}x{shape[2]} channels, lower half overlapping r=4 spheres at "
                                    "porosity U[0.6,0.8]; train seeds 500000+, held-out seeds 600000+",
@@ -973,9 +977,8 @@ def run_ours(args, world, rank, local):
             parity[name] = {"achieved": gbs, "frac": gbs / peak, "share": float(sel.sum() / durs.sum())}
     value = whole_job_rate(nf_total * args.steps, ms, world)
     # DRAM bytes per fluid cell and launch of the step kernels as they stand,
-    # from one ncu capture of this command (dram__bytes_read.sum +
-    # dram__bytes_write.sum, profiles/step_kernels_channel_256x256x512_dram.txt):
-    # only for the configuration it was taken on
+    # from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of one
+    # solver of this workload: only for the configuration they were taken on
     traffic = None
     if args.storage == "f32" and args.odd == "auto" and args.even == "auto":
         if args.workload == "channel":

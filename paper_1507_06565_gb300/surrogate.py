@@ -133,34 +133,56 @@ def predict(params, case: Channel, geom=None):
     return u[0]
 
 
+def relaxation_steps(case: Channel) -> float:
+    """Decay time (steps) of the slowest viscous mode between the walls:
+    nz^2 / (pi^2 nu)."""
+    nu = (case.tau - 0.5) / 3.0
+    return case.nz ** 2 / (np.pi ** 2 * nu)
+
+
 def time_to_steady(case: Channel, u0=None, tol=1e-8, interval=500, max_steps=2_000_000, geom=None,
-                   flags=WALL_FLAGS) -> dict:
+                   flags=WALL_FLAGS, ref_steps=0) -> dict:
     """Run one case to the plane-profile tolerance from rest (u0 None) or from
-    a predicted field; wall time includes the solver set-up."""
+    a predicted field; wall time includes the solver set-up.  With ref_steps,
+    the converged run then continues for that many steps outside the timed
+    part and reports the permeability it reaches there (the reference the
+    converged permeabilities are judged against)."""
     import torch
 
     geom = geom or lbm_geometry_from_spheres(*case.sphere_args())
+    window = (2, case.nz // 2 - 8)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s = Solver(geom, case.tau, case.lam, case.g, u0=u0, flags=flags)
     rc, steps, res = s.run_until(tol, interval, max_steps, criterion="profile")
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    return {"status": rc, "steps": steps, "residual": res, "seconds": secs,
-            "permeability": s.permeability(2, case.nz // 2 - 8)}
+    out = {"status": rc, "steps": steps, "residual": res, "seconds": secs, "permeability": s.permeability(*window)}
+    if ref_steps > 0 and rc == 0:
+        s.step(int(ref_steps))
+        out["ref_steps"] = int(ref_steps)
+        out["permeability_ref"] = s.permeability(*window)
+    return out
 
 
-def warm_vs_cold(params, seeds, shape=(64, 64, 128), tol=1e-8, interval=500) -> list:
+def warm_vs_cold(params, seeds, shape=(64, 64, 128), tol=1e-8, interval=500, ref_relaxations=4.0) -> list:
     """For each held-out seed: cold start, and warm start from the network
     (inference time counted).  The permeability window is the porous layer
-    away from the interface."""
+    away from the interface.
+
+    A profile residual of 1e-8 (relative to the free channel's velocity) still
+    leaves the slow porous-layer velocities some way from steady, so the
+    permeability of either run is judged against a reference: the cold run
+    continued, untimed, for ref_relaxations decay times of the slowest
+    viscous mode (each one cuts the remaining error by e)."""
     import torch
 
     rows = []
     for sd in seeds:
         case = channel_case(sd, shape)
         geom = lbm_geometry_from_spheres(*case.sphere_args())
-        cold = time_to_steady(case, None, tol, interval, geom=geom)
+        ref_steps = int(np.ceil(ref_relaxations * relaxation_steps(case) / interval)) * interval
+        cold = time_to_steady(case, None, tol, interval, geom=geom, ref_steps=ref_steps)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         u0 = predict(params, case, geom).contiguous()
@@ -168,6 +190,9 @@ def warm_vs_cold(params, seeds, shape=(64, 64, 128), tol=1e-8, interval=500) -> 
         warm = time_to_steady(case, u0, tol, interval, geom=geom)
         warm["seconds"] += infer
         warm["inference_s"] = infer
+        k_ref = cold.get("permeability_ref", cold["permeability"])
         rows.append({"seed": sd, "porosity": case.porosity, "cold": cold, "warm": warm,
-                     "k_rel_diff": abs(warm["permeability"] / cold["permeability"] - 1.0)})
+                     "k_rel_diff": abs(warm["permeability"] / cold["permeability"] - 1.0),
+                     "k_err_cold": abs(cold["permeability"] / k_ref - 1.0),
+                     "k_err_warm": abs(warm["permeability"] / k_ref - 1.0)})
     return rows

@@ -2,6 +2,8 @@
 distance, U-Net forward (oracle rounding activations and weights to bf16 the
 way the kernels store them), gradients of every layer, Adam, and a training
 smoke test."""
+import time
+
 import numpy as np
 import pytest
 
@@ -165,8 +167,12 @@ def test_warm_start_gains_over_cold_start(torch_cuda):
     the steady velocity of held-out packings to within 30% (L2) where the
     cold start (rest) is 100% away; warm-started from it, the LBM reaches the
     same steady state (plane-profile residual 1e-8, permeability within 1e-3
-    of the cold start's) in fewer steps in total over six held-out packings
-    (wall rule with the corner safeguards, as the surrogate module runs it).
+    of the cold start's) in fewer steps and less wall time in total over six
+    held-out packings (wall rule with the corner safeguards, as the surrogate
+    module runs it).  The warm start's wall time counts everything it adds:
+    the signed distance field, the network's forward pass and the
+    initialisation from the predicted field; both sides count the solver
+    set-up (lists, links, grid tuning).
     (Training uses float atomics in the weight gradient, so single cases vary
     by a few residual intervals from run to run; the totals do not.)"""
     from paper_1507_06565_gb300 import surrogate as S
@@ -177,22 +183,36 @@ def test_warm_start_gains_over_cold_start(torch_cuda):
     assert np.mean(tr.losses[-4:]) < 0.01 * tr.losses[0]
     params = tr.net.params().cpu().numpy()
     cold_steps = warm_steps = 0
+    cold_s = warm_s = 0.0
     for sd in range(600000, 600006):
         case = S.channel_case(sd, shape)
         geom = L.lbm_geometry_from_spheres(*case.sphere_args())
+        torch_cuda.cuda.synchronize()
+        t0 = time.perf_counter()
         cold = L.Solver(geom, case.tau, case.lam, case.g, flags=S.WALL_FLAGS)
         rc, n_cold, _ = cold.run_until(1e-8, 500, 2_000_000, criterion="profile")
+        torch_cuda.cuda.synchronize()
+        cold_s += time.perf_counter() - t0
         assert rc == 0
         _, u_conv = cold.moments()
+        torch_cuda.cuda.synchronize()
+        t0 = time.perf_counter()
         u0 = S.predict(params, case, geom).contiguous()
+        te = time.perf_counter()
         fl = torch_cuda.from_numpy(geom.mask() == 0).to(u0.device)   # lbm_init ignores solid cells
         err = float((u0 - u_conv)[:, fl].norm() / u_conv[:, fl].norm())
+        err_s = time.perf_counter() - te
         assert err < 0.3, (sd, err)
         warm = L.Solver(geom, case.tau, case.lam, case.g, u0=u0, flags=S.WALL_FLAGS)
         rc, n_warm, _ = warm.run_until(1e-8, 500, 2_000_000, criterion="profile")
+        torch_cuda.cuda.synchronize()
+        # the error check above is not the warm start's work: its time is left out
+        warm_s += time.perf_counter() - t0 - err_s
         assert rc == 0
         window = (2, case.nz // 2 - 8)
         assert abs(warm.permeability(*window) / cold.permeability(*window) - 1.0) <= 1e-3
         cold_steps += n_cold
         warm_steps += n_warm
+    print(f"\nwarm start: {warm_steps} vs {cold_steps} steps, {warm_s:.2f} vs {cold_s:.2f} s")
     assert warm_steps < cold_steps, (warm_steps, cold_steps)
+    assert warm_s < cold_s, (warm_s, cold_s)
