@@ -105,18 +105,12 @@ __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
     float h[kQ];
 #pragma unroll
     for (int k = 0; k < kQ; ++k) h[k] = ld_raw(p.pdf + k * n_pad + i);
-    if (REF && rr >= 0) {
-#pragma unroll
-        for (int k = 0; k < kQ; ++k) h[k] = __fadd_rn(h[k], __ldg(p.ref_rd + rr + k));
-    }
+    if (REF && rr >= 0) ref_rows<true, 0, sizeof(T) == 2>(h, p.ref_rd + rr);
     if (m) cli_links<true>(h, p.link_a, off, m);
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
     if (m) cli_links<false>(h, p.link_a, off, m);
-    if (REF && rr >= 0) {
-#pragma unroll
-        for (int k = 0; k < kQ; ++k) h[k] = __fsub_rn(h[k], __ldg(p.ref_wr + rr + k));
-    }
+    if (REF && rr >= 0) ref_rows<false, 0, sizeof(T) == 2>(h, p.ref_wr + rr);
 #pragma unroll
     for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
 }
@@ -179,18 +173,12 @@ __device__ __forceinline__ void odd_cell(const StepArgs<T> &p, int32_t i, int32_
     // reference rows: the slot read for h_k belongs to x - e_k (plane z - ez_k),
     // the slot written with h_k to x + e_k (plane z + ez_k)
     const int32_t rr = ref_row<REF>(p, i);
-    if (REF && rr >= 0) {
-#pragma unroll
-        for (int k = 0; k < kQ; ++k) h[k] = __fadd_rn(h[k], __ldg(p.ref_rd + rr - ez(k) * kRefStride + k));
-    }
+    if (REF && rr >= 0) ref_rows<true, -1, sizeof(T) == 2>(h, p.ref_rd + rr);
     if (m) cli_links<true>(h, p.link_a, off, m);
     if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
     collide(h, p.c);
     if (m) cli_links<false>(h, p.link_a, off, m);
-    if (REF && rr >= 0) {
-#pragma unroll
-        for (int k = 0; k < kQ; ++k) h[k] = __fsub_rn(h[k], __ldg(p.ref_wr + rr + ez(k) * kRefStride + k));
-    }
+    if (REF && rr >= 0) ref_rows<false, 1, sizeof(T) == 2>(h, p.ref_wr + rr);
     st_raw(p.pdf + ui, h[0]);
 #pragma unroll
     for (int k = 1; k < kQ; ++k) st_raw(p.pdf + slot(k), h[k]);
@@ -263,18 +251,12 @@ __global__ void __launch_bounds__(kBlock, MINB) k_step_even_bulk(StepArgs<T> p)
         if (t < 32 && j + S < count) issue(j + S);
         if (!live) continue;
         const int32_t rr = ref_row<REF>(p, i);
-        if (REF && rr >= 0) {
-#pragma unroll
-            for (int k = 0; k < kQ; ++k) h[k] = __fadd_rn(h[k], __ldg(p.ref_rd + rr + k));
-        }
+        if (REF && rr >= 0) ref_rows<true, 0, sizeof(T) == 2>(h, p.ref_rd + rr);
         if (m) cli_links<true>(h, p.link_a, off, m);
         if (p.shift_on) apply_shift(h, part_shift_of(p, i) * StoreScale<T>::v);
         collide(h, p.c);
         if (m) cli_links<false>(h, p.link_a, off, m);
-        if (REF && rr >= 0) {
-#pragma unroll
-            for (int k = 0; k < kQ; ++k) h[k] = __fsub_rn(h[k], __ldg(p.ref_wr + rr + k));
-        }
+        if (REF && rr >= 0) ref_rows<false, 0, sizeof(T) == 2>(h, p.ref_wr + rr);
 #pragma unroll
         for (int k = 0; k < kQ; ++k) st_raw(p.pdf + opp(k) * n_pad + i, h[k]);
     }
