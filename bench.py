@@ -38,7 +38,7 @@ WORKLOAD = ("256x256x512 channel, walls z=0/511, porous layer z<256 of overlappi
 # neighbour table outside the dense tiles): ncu on one full-size solver of the
 # sweep (porosity 0.6, 26.7 M fluid cells), applied per fluid cell to all four
 # (profiles/step_kernels_channel_256x256x512_phi06_dram.txt)
-MEASURED_DRAM_B_PER_FLUP = {"even": 155.5, "odd": 180.3}
+MEASURED_DRAM_B_PER_FLUP = {"even": 153.1, "odd": 180.3}
 # the same for the batched REV cubes (table-only odd step), taken on the first
 # 8 cubes (11.2 M fluid cells, far above L2) and applied per fluid cell to the
 # 64-cube batch (profiles/step_kernels_rev_8cubes_dram.txt)

@@ -92,12 +92,16 @@ __device__ __forceinline__ float part_shift_of(const StepArgs<T> &p, int32_t i)
 // With reference populations (REF, a tile in or next to referenced planes),
 // the population of direction k is read as slot + R_k(z) and written as
 // f~_k - R_k(z), z the plane of the slot's owner (the cell itself in the even
-// step).  Dense tiles have no wall links.
+// step).  Dense tiles have no wall links, so in FP32 storage, where the step
+// is bound by its bytes, their cells skip the link-mask load (4 B per cell;
+// the tile's descriptor is one broadcast load per warp).
 template <typename T, bool REF>
 __device__ __forceinline__ void even_cell(const StepArgs<T> &p, int32_t i)
 {
     const bool live = i < p.n_fluid;
-    const uint32_t m = live ? p.lmask[i] & kLinkBits : 0u;
+    const int32_t tile = i / kBlock;
+    const bool dense = sizeof(T) == 4 && tile >= p.dense_lo && tile < p.dense_hi && __ldg(p.tile_desc + tile).x >= 0;
+    const uint32_t m = live && !dense ? p.lmask[i] & kLinkBits : 0u;
     const uint32_t off = first_link(p.warp_off, i, m);
     if (!live) return;
     const int32_t rr = ref_row<REF>(p, i);
