@@ -170,8 +170,9 @@ def warm_vs_cold(params, seeds, shape=(64, 64, 128), tol=1e-8, interval=500, ref
     (inference time counted).  The permeability window is the porous layer
     away from the interface.
 
-    A profile residual of 1e-8 (relative to the free channel's velocity) still
-    leaves the slow porous-layer velocities some way from steady, so the
+    A profile residual of 1e-8 (relative to the profile's norm, which the free
+    channel dominates) can still leave the slow porous-layer velocities some
+    way from steady, so the
     permeability of either run is judged against a reference: the cold run
     continued, untimed, for ref_relaxations decay times of the slowest
     viscous mode (each one cuts the remaining error by e)."""
