@@ -1058,7 +1058,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--odd", choices=["auto", "table", "rows", "staged", "derived"], default="auto",
                     help="neighbour indices of the odd step (library default, int32 table, row bitmasks, row words "
-                         "staged per tile)")
+                         "staged per tile, x-neighbours derived from the table's other entries)")
     ap.add_argument("--even", choices=["auto", "staged"], default="auto",
                     help="even-step kernel: autotuned, or always the TMA-staged one")
     ap.add_argument("--bounce-back", action="store_true",
