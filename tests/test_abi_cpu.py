@@ -78,6 +78,37 @@ def test_explicit_list_geometry(lib):
     assert np.array_equal(geom.spheres(), sp)
 
 
+# hand-made sphere lists: a centre on grid points (cells at exactly distance r
+# are solid: the test is |x - c|^2 <= r^2), spheres across the periodic x and
+# y faces, two overlapping spheres, a sphere cut by the bottom wall layer and
+# one reaching into the top wall layer
+HAND_CASES = {
+    "on grid points": (9, 9, 12, [[4.0, 4.0, 6.0, 3.0]]),
+    "across periodic faces": (10, 9, 12, [[-0.25, 8.75, 5.5, 2.25], [9.9, 0.1, 6.0, 1.5]]),
+    "two overlapping": (12, 10, 12, [[4.5, 5.0, 6.0, 3.0], [7.0, 5.0, 6.5, 2.5]]),
+    "cut by the walls": (8, 8, 10, [[4.0, 4.0, 0.5, 2.75], [3.5, 3.5, 9.25, 1.5]]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(HAND_CASES))
+def test_hand_made_geometries_bit_exact(lib, name):
+    nx, ny, nz, sp = HAND_CASES[name]
+    sp = np.array(sp)
+    geom = L.lbm_geometry_from_list(nx, ny, nz, False, sp)
+    mask = geom.mask()
+    assert np.array_equal(mask, O.voxelize(nx, ny, nz, False, sp))
+    assert np.array_equal(geom.spheres(), sp)
+    # brute force from the definition: solid where some periodic image (in x
+    # and y) of a sphere holds the cell centre, or in the wall layers z = 0, nz - 1
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    solid = (z == 0) | (z == nz - 1)
+    for cx, cy, cz, r in sp:
+        for sx in (-nx, 0, nx):
+            for sy in (-ny, 0, ny):
+                solid |= (x - cx - sx) ** 2 + (y - cy - sy) ** 2 + (z - cz) ** 2 <= r * r
+    assert np.array_equal(mask.astype(bool), solid)
+
+
 def test_error_codes(lib):
     with pytest.raises(L.LBMError) as e:
         L.lbm_geometry_from_spheres(24, 24, 24, True, 0.0, 24.0, 4.0, 4.0, 0.1, False, 3, max_rejects=2000)
